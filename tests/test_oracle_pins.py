@@ -1,0 +1,444 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these checks re-types the oracle's own formulas: each compares the
+oracle with an independent fact -- a library quadrature or polynomial routine,
+a moment identity derived by integration by parts, a formula PRINTED in the
+paper (where the oracle uses the defining series instead), a conservation law,
+a closed-form flow solution, or the paper's printed lattice constant.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial import hermite_e as He
+
+import oracle
+from paper_2302_04741_gb300 import workloads as W
+
+LATS = [(oracle.D2Q37, 9), (oracle.D3Q39, 7)]
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dfact(n):
+    r = 1
+    for k in range(n - 1, 0, -2):
+        r *= k
+    return r
+
+
+def gauss_moment(alpha):
+    """E[prod Z_a^alpha_a] for a standard normal vector Z."""
+    r = 1
+    for a in alpha:
+        if a % 2:
+            return 0
+        r *= dfact(a)
+    return r
+
+
+def gauss_expect(D, fn, npts=10):
+    """E[fn(Z)] over Z ~ N(0, I_D) by numpy's probabilists' Gauss-Hermite rule
+    (exact for polynomials of degree <= 2*npts - 1 per axis)."""
+    z, wz = He.hermegauss(npts)
+    wz = wz / math.sqrt(2.0 * math.pi)
+    tot = 0.0
+    for idx in itertools.product(range(npts), repeat=D):
+        pt = np.array([z[k] for k in idx])
+        wt = np.prod([wz[k] for k in idx])
+        tot = tot + wt * fn(pt)
+    return tot
+
+
+def he_product(x, idx, D):
+    """Tensor Hermite polynomial as the product of 1-D He_n (numpy): the
+    multi-index counts how often each axis occurs."""
+    r = 1.0
+    for a in range(D):
+        k = idx.count(a)
+        r *= He.hermeval(x[a], [0] * k + [1])
+    return r
+
+
+def maxwell_moment(rho, u, theta, alpha):
+    """rho * E[prod (u_a + sqrt(theta) Z_a)^alpha_a]: raw moment of the Maxwellian."""
+    D = len(alpha)
+    return rho * gauss_expect(D, lambda z: np.prod([(u[a] + math.sqrt(theta) * z[a]) ** alpha[a]
+                                                    for a in range(D)]), npts=6)
+
+
+CASES = [(1.0, (0.0, 0.0, 0.0), 1.0), (0.93, (0.11, -0.07, 0.05), 1.08),
+         (1.12, (-0.21, 0.13, -0.02), 0.87)]
+
+
+# ---------------------------------------------------------------- (a) lattice
+@pytest.mark.parametrize("lat,deg", LATS)
+def test_quadrature_exact_to_degree(lat, deg):
+    """Sum_i w_i p(xi_i) = int omega p for every monomial of degree <= Q (the
+    quadrature identity of Sec. 2), and fails for some monomial of degree Q+1."""
+    D, Q, c, e, w, _ = oracle.lattice_info(lat)
+    xi = c * e[:, :D].astype(float)
+    assert np.all(w > 0) and abs(w.sum() - 1.0) < 1e-15
+    for alpha in itertools.product(range(deg + 1), repeat=D):
+        if sum(alpha) > deg:
+            continue
+        s = np.sum(w * np.prod(xi ** np.array(alpha), axis=1))
+        exact = gauss_moment(alpha)
+        assert abs(s - exact) <= 2e-14 * max(1.0, exact), (alpha, s, exact)
+    worst = 0.0
+    for alpha in itertools.product(range(deg + 2), repeat=D):
+        if sum(alpha) != deg + 1:
+            continue
+        s = np.sum(w * np.prod(xi ** np.array(alpha), axis=1))
+        worst = max(worst, abs(s - gauss_moment(alpha)))
+    assert worst > 1e-3
+
+
+def test_d2q37_lattice_constant_matches_paper():
+    """c ~ 1.19698 (Sec. 3.1)."""
+    with open(os.path.join(GOLDEN, "d2q37_lattice_constant.txt")) as fh:
+        vals = dict(line.split() for line in fh if line.strip() and not line.startswith("#"))
+    c_paper = float(vals["c"])
+    _, Q, c, e, _, _ = oracle.lattice_info(oracle.D2Q37)
+    assert Q == 37
+    assert abs(c - c_paper) < 5e-6
+    # the velocity set is symmetric: every e has its opposite
+    s = {tuple(v) for v in e}
+    assert all(tuple(-np.array(v)) in s for v in s)
+
+
+# ------------------------------------------------- Hermite algebra (Sec. 2)
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_hermite_tensors_are_products_of_1d_hermite(D):
+    rng = np.random.default_rng(10 + D)
+    for _ in range(4):
+        x = rng.normal(size=D)
+        for n in range(5):
+            H = oracle.hermite_tensor(D, n, x)
+            for idx in itertools.product(range(D), repeat=n):
+                ref = he_product(x, idx, D)
+                val = H[idx] if n else H
+                assert abs(val - ref) < 1e-12 * (1 + abs(ref)), (n, idx)
+
+
+@pytest.mark.parametrize("D", [2, 3])
+@pytest.mark.parametrize("rho,u,theta", CASES)
+def test_maxwell_coefficients_by_quadrature(D, rho, u, theta):
+    """a^(n)_0 = int f0 H^(n) dxi (Eq. an with f = f0), integrated numerically."""
+    u = np.array(u[:D])
+    for n in range(5):
+        A = oracle.maxwell_coeff(D, n, rho, u, theta)
+        for idx in itertools.product(range(D), repeat=n):
+            ref = rho * gauss_expect(D, lambda z: he_product(u + math.sqrt(theta) * z, idx, D),
+                                     npts=4)
+            val = A[idx] if n else A
+            assert abs(val - ref) < 1e-12, (n, idx, val, ref)
+
+
+@pytest.mark.parametrize("lat,deg", LATS)
+@pytest.mark.parametrize("rho,u,theta", CASES)
+def test_discrete_equilibrium_moments(lat, deg, rho, u, theta):
+    """Moments of f0_i up to the expansion order equal the Maxwellian's raw
+    moments (Eq. an1 with the degree-Q rule)."""
+    D, Q, c, e, w, neq = oracle.lattice_info(lat)
+    xi = c * e[:, :D].astype(float)
+    u = np.array(u[:D])
+    feq = oracle.equilibrium(lat, rho, u, theta)
+    for alpha in itertools.product(range(neq + 1), repeat=D):
+        if sum(alpha) > neq:
+            continue
+        s = np.sum(feq * np.prod(xi ** np.array(alpha), axis=1))
+        ref = maxwell_moment(rho, u, theta, alpha)
+        assert abs(s - ref) < 1e-13 * max(1.0, abs(ref)), (alpha, s, ref)
+
+
+# ------------------------------------------------- (b) force term (Sec. 2)
+def truncated_second_moment(order, rho, u, theta, D):
+    """int f_N xi_b xi_c for the Hermite series truncated at order N."""
+    if order >= 2:
+        return rho * (np.outer(u, u) + theta * np.eye(D))
+    return rho * np.eye(D)
+
+
+@pytest.mark.parametrize("lat,deg", LATS)
+@pytest.mark.parametrize("order", [0, 1, 2])
+@pytest.mark.parametrize("rho,u,theta", CASES)
+def test_force_moments(lat, deg, order, rho, u, theta):
+    """Moments of F = -g . grad_xi f_N, by integration by parts:
+    int F xi^alpha = sum_k g_{alpha_k} int f_N xi^{alpha minus k}."""
+    D, Q, c, e, w, _ = oracle.lattice_info(lat)
+    xi = c * e[:, :D].astype(float)
+    u = np.array(u[:D])
+    g = np.array([0.013, -0.021, 0.008][:D])
+    F = oracle.force(lat, order, rho, u, theta, g)
+    assert abs(F.sum()) < 1e-15
+    np.testing.assert_allclose(F @ xi, rho * g, atol=1e-15)
+    m2 = np.einsum("i,ia,ib->ab", F, xi, xi)
+    ref2 = rho * (np.outer(g, u) + np.outer(u, g)) if order >= 1 else np.zeros((D, D))
+    np.testing.assert_allclose(m2, ref2, atol=2e-15)
+    m3 = np.einsum("i,ia,ib,ic->abc", F, xi, xi, xi)
+    S = truncated_second_moment(order, rho, u, theta, D)
+    ref3 = (np.einsum("a,bc->abc", g, S) + np.einsum("b,ac->abc", g, S)
+            + np.einsum("c,ab->abc", g, S))
+    np.testing.assert_allclose(m3, ref3, atol=5e-15)
+    # heat production int F c^2 (Eq. F-heat): zero once the n = 2 term is kept
+    cc = xi - u
+    heat = np.sum(F * np.sum(cc * cc, axis=1))
+    if order >= 1:
+        assert abs(heat) < 2e-15
+    else:
+        assert abs(heat - (-2.0 * rho * g @ u)) < 2e-15
+
+
+@pytest.mark.parametrize("lat,deg", LATS)
+@pytest.mark.parametrize("rho,u,theta", CASES)
+def test_force_matches_printed_expansions(lat, deg, rho, u, theta):
+    """The oracle evaluates Eq. F as a tensor series; the paper prints its
+    expanded forms: the second-order form after Eq. F, and Eq. fi (third moment,
+    with its sigma terms).  The bracket -w rho (g.u)(u.xi) of Eq. fi belongs to
+    the n = 3 term (it is half of -2 (g.u)(u.xi) in Eq. f3)."""
+    D, Q, c, e, w, _ = oracle.lattice_info(lat)
+    xi = c * e[:, :D].astype(float)
+    u = np.array(u[:D])
+    g = np.array([0.013, -0.021, 0.008][:D])
+    gx, ux, x2 = xi @ g, xi @ u, np.sum(xi * xi, axis=1)
+    gu, u2 = g @ u, u @ u
+    second = w * rho * (gx + gx * ux - gu)
+    np.testing.assert_allclose(oracle.force(lat, 1, rho, u, theta, g), second, atol=1e-16)
+    third = (w * rho * gx * (1 + ux + 0.5 * (ux ** 2 - u2 + (theta - 1) * (x2 - D - 2)))
+             - w * rho * gu * (1 + ux))
+    np.testing.assert_allclose(oracle.force(lat, 2, rho, u, theta, g), third, atol=1e-16)
+    # sigma terms: -(w/2)[(g.xi) sigma:xi xi - 2 sigma:g xi], sigma symmetric traceless
+    rng = np.random.default_rng(5)
+    s = rng.normal(size=(D, D)) * 1e-3
+    s = s + s.T
+    s -= np.trace(s) / D * np.eye(D)
+    sxx = np.einsum("ab,ia,ib->i", s, xi, xi)
+    sgx = np.einsum("ab,a,ib->i", s, g, xi)
+    with_sigma = third - 0.5 * w * (gx * sxx - 2.0 * sgx)
+    np.testing.assert_allclose(oracle.force(lat, 2, rho, u, theta, g, sigma=s), with_sigma,
+                               atol=1e-16)
+
+
+# ------------------------------------------ time stepping (Eq. lbm) helpers
+def make_sim(lat, shape, tau, g, order=2, bc=(0, 0, 0), T_lo=(1, 1, 1), T_hi=(1, 1, 1),
+             sigma=False):
+    return oracle.OracleSim(lat, *shape, tau, g, force_order=order, include_sigma=sigma, bc=bc,
+                            T_lo=T_lo, T_hi=T_hi)
+
+
+def smooth_random_state(lat, shape, seed, amp_u=0.02, amp_T=0.03):
+    D = W.dims(lat)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    rho = 1.0 + 0.01 * (W.uniform(seed, 11, N) - 0.5)
+    u = 2 * amp_u * (W.uniform(seed, 12, D * N).reshape(D, N) - 0.5)
+    T = 1.0 + 2 * amp_T * (W.uniform(seed, 13, N) - 0.5)
+    return rho, u, T
+
+
+def pulled_sums(sim):
+    ft = sim.pulled()
+    xi = sim.c * sim.e[:, :sim.D].astype(float)
+    mass = ft.sum()
+    mom = np.einsum("in,ia->a", ft, xi)
+    en = np.einsum("in,i->", ft, np.sum(xi * xi, axis=1))
+    return mass, mom, en
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (7, 5, 1)), (oracle.D3Q39, (4, 5, 3))])
+@pytest.mark.parametrize("order", [1, 2])
+def test_budgets_per_step(lat, shape, order):
+    """(c): per step, total momentum changes by exactly sum rho g and total
+    energy sum f xi^2 by sum 2 rho g.u (mid-point u); mass is unchanged."""
+    D = W.dims(lat)
+    N = shape[0] * shape[1] * shape[2]
+    g = 1e-3 * (W.uniform(7, 14, D * N).reshape(D, N) - 0.5)
+    sim = make_sim(lat, shape, 0.7, g, order=order)
+    sim.init(*smooth_random_state(lat, shape, 3))
+    sim.step(2)
+    for _ in range(3):
+        m0, p0, e0 = pulled_sums(sim)
+        rho, u, _, _ = sim.moments()
+        sim.step(1)
+        m1, p1, e1 = pulled_sums(sim)
+        assert abs(m1 - m0) < 1e-13 * m0
+        np.testing.assert_allclose(p1 - p0, (rho * g).sum(axis=1), rtol=1e-9, atol=1e-15 * m0)
+        assert abs((e1 - e0) - 2.0 * np.sum(rho * np.sum(g * u, axis=0))) < 1e-13 * e0
+
+
+@pytest.mark.parametrize("lat,shape,bc", [
+    (oracle.D2Q37, (5, 4, 1), (0, 0, 0)),
+    (oracle.D2Q37, (4, 9, 1), (0, 1, 0)),
+    (oracle.D3Q39, (3, 4, 7), (0, 0, 1)),
+])
+def test_init_then_moments_roundtrip(lat, shape, bc):
+    """After init the pulled state reproduces the requested rho, u, T."""
+    D = W.dims(lat)
+    N = shape[0] * shape[1] * shape[2]
+    g = 1e-3 * (W.uniform(8, 14, D * N).reshape(D, N) - 0.5)
+    sim = make_sim(lat, shape, 0.8, g, bc=bc)
+    rho, u, T = smooth_random_state(lat, shape, 4)
+    sim.init(rho, u, T)
+    r2, u2, T2, q2 = sim.moments()
+    np.testing.assert_allclose(r2, rho, atol=1e-14)
+    np.testing.assert_allclose(u2, u, atol=1e-14)
+    np.testing.assert_allclose(T2, T, atol=1e-14)
+    assert np.max(np.abs(q2)) < 1e-14  # a Maxwellian carries no heat flux
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (6, 5, 1)), (oracle.D3Q39, (3, 4, 5))])
+def test_uniform_state_is_fixed_point(lat, shape):
+    D = W.dims(lat)
+    N = shape[0] * shape[1] * shape[2]
+    sim = make_sim(lat, shape, 0.6, np.zeros((D, N)))
+    u0 = np.array([0.05, -0.03, 0.02][:D])
+    sim.init(np.full(N, 1.02), np.repeat(u0[:, None], N, axis=1), np.full(N, 0.95))
+    sim.step(10)
+    rho, u, T, q = sim.moments()
+    np.testing.assert_allclose(rho, 1.02, atol=1e-14)
+    np.testing.assert_allclose(u, np.repeat(u0[:, None], N, axis=1), atol=1e-14)
+    np.testing.assert_allclose(T, 0.95, atol=1e-14)
+
+
+def test_translation_invariance():
+    """Rolling the initial fields and the force rolls the result exactly."""
+    lat, shape = oracle.D2Q37, (8, 6, 1)
+    N = 48
+    g = 1e-3 * (W.uniform(9, 14, 2 * N).reshape(2, N) - 0.5)
+    rho, u, T = smooth_random_state(lat, shape, 5)
+    a = make_sim(lat, shape, 0.75, g)
+    a.init(rho, u, T)
+    a.step(4)
+
+    def roll(v, k=(2, 3)):
+        v = np.asarray(v)
+        return np.roll(v.reshape(v.shape[:-1] + (6, 8)), k, axis=(-2, -1)).reshape(v.shape)
+
+    b = make_sim(lat, shape, 0.75, roll(g))
+    b.init(roll(rho), roll(u), roll(T))
+    b.step(4)
+    for x, y in zip(a.moments(), b.moments()):
+        np.testing.assert_array_equal(roll(x), y)
+
+
+@pytest.mark.parametrize("bc", [1, 2])
+def test_walls_conserve_mass(bc):
+    """Half-way bounce-back is a bijection of slots and the thermal wall returns
+    each column's outgoing mass, so mass is conserved (per column for the
+    thermal wall)."""
+    lat, shape = oracle.D2Q37, (5, 8, 1)
+    N = 40
+    g = np.zeros((2, N))
+    g[1] = -1e-3
+    g[0] = 2e-4
+    sim = make_sim(lat, shape, 0.7, g, bc=(0, bc, 0), T_lo=(1, 1.1, 1), T_hi=(1, 0.9, 1))
+    rho, u, T = smooth_random_state(lat, shape, 6)
+    sim.init(rho, u, T)
+    m0 = sim.pulled().sum()
+    sim.step(25)
+    m1 = sim.pulled().sum()
+    assert abs(m1 - m0) < 1e-13 * m0
+
+
+def test_step_sites_equals_full_step():
+    lat, shape = oracle.D2Q37, (6, 7, 1)
+    N = 42
+    g = 1e-3 * (W.uniform(10, 14, 2 * N).reshape(2, N) - 0.5)
+    sim = make_sim(lat, shape, 0.9, g, bc=(0, 2, 0), T_lo=(1, 1.05, 1), T_hi=(1, 0.95, 1))
+    sim.init(*smooth_random_state(lat, shape, 7))
+    sim.step(3)
+    st = sim.get_state()
+    sites = np.array([0, 5, 17, 41])
+    out = sim.step_sites(st, sites)
+    sim.step(1)
+    np.testing.assert_array_equal(sim.get_state()[:, sites].T, out)
+
+
+# ------------------------------------ (d) Kolmogorov flow, transient closed form
+@pytest.mark.slow
+def test_kolmogorov_amplitude():
+    """u_x(y, t) = U (1 - exp(-nu k^2 t)) sin(k y), U = g0 L^2 / (4 pi^2 nu),
+    with nu = theta (tau - 1/2), L = n_y c (lattice spacing c, Sec. 3.1)."""
+    n, tau, g0, steps = 64, 0.8, 1e-5, 2000
+    w = W.kolmogorov(nx=n, ny=n, tau=tau, g0=g0, rho_noise=0.0, T_amp=0.0)
+    g = W.g_field_array(w["lattice"], w["shape"], w["g"])
+    sim = make_sim(oracle.D2Q37, w["shape"], tau, g)
+    sim.init(w["rho"], w["u"], w["T"])
+    sim.step(steps)
+    _, u, _, _ = sim.moments()
+    ux = u[0].reshape(n, n)  # [y][x]
+    y = np.arange(n)
+    s = np.sin(2 * np.pi * y / n)
+    amp = np.mean(ux, axis=1) @ s / (s @ s)
+    c = sim.c
+    L = n * c
+    nu = 1.0 * (tau - 0.5)
+    k = 2 * np.pi / L
+    U = g0 * L ** 2 / (4 * np.pi ** 2 * nu)
+    ref = U * (1 - np.exp(-nu * k * k * steps))
+    assert abs(amp / ref - 1) < 5e-3, (amp, ref)
+    assert np.max(np.abs(u[1])) < 1e-3 * ref
+
+
+# --------------------------------- (e) spurious heat flux of the N = 1 force
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (4, 4, 1)), (oracle.D3Q39, (4, 4, 4))])
+@pytest.mark.parametrize("u0,theta0", [((0.0, 0.0, 0.0), 1.1), ((0.1, 0.05, -0.05), 1.0),
+                                       ((0.2, -0.1, 0.05), 0.9), ((0.15, 0.0, 0.1), 1.1)])
+def test_spurious_heat_flux(lat, shape, u0, theta0):
+    """Homogeneous periodic box under uniform g.  With the third-moment term
+    (force order 2) the heat flux vanishes; without it (order 1) it equals the
+    Chapman-Enskog error q_err = -rho tau/2 {[u^2 + (theta-1)(D+2)] g + 2 (g.u) u}
+    with tau = tau-hat - 1/2 (Sec. 2)."""
+    D = W.dims(lat)
+    N = shape[0] * shape[1] * shape[2]
+    tau = 0.8
+    # first-order Chapman-Enskog omits the O(tau^2 g^2 u) lag of the state
+    # accelerating at du/dt = g; with |g| ~ 1e-6 it stays below 1e-5 relative.
+    g0 = np.array([1e-6, -2e-6, 1.5e-6][:D])
+    g = np.repeat(g0[:, None], N, axis=1)
+    u0 = np.array(u0[:D])
+    for order in (1, 2):
+        sim = make_sim(lat, shape, tau, g, order=order)
+        sim.init(np.ones(N), np.repeat(u0[:, None], N, axis=1), np.full(N, theta0))
+        sim.step(int(30 / tau) + 10)
+        rho, u, T, q = sim.moments()
+        uu, th, r = u[:, 0], T[0], rho[0]
+        ref = -0.5 * r * (tau - 0.5) * ((uu @ uu + (th - 1) * (D + 2)) * g0 + 2 * (g0 @ uu) * uu)
+        if order == 2:
+            assert np.max(np.abs(q)) < 1e-13  # round-off; q_err is ~1e-6 here
+        else:
+            scale = max(np.max(np.abs(ref)), 1e-12)
+            assert np.max(np.abs(q[:, 0] - ref)) < 1e-4 * scale + 1e-16, (q[:, 0], ref)
+            np.testing.assert_allclose(q, np.repeat(q[:, :1], N, axis=1), atol=1e-17)
+
+
+# ------------------------ thermal walls: steady conduction between two walls
+@pytest.mark.slow
+def test_thermal_wall_conduction():
+    """No gravity, walls at 1.05 (low) and 0.95 (high).  In the bulk the steady
+    state has no flow, uniform pressure rho*theta, a linear temperature falling
+    from the low wall toward the high wall, and a uniform heat flux obeying
+    Fourier's law q = -lambda dtheta/dy with lambda = c_p mu, c_p = (D+2)/2 and
+    mu = p tau, tau = tau-hat - 1/2 (Pr = 1 for BGK, Sec. 3.1).  This pins the
+    thermal wall's orientation and the heat-flux diagnostic."""
+    lat, nx, ny, tau = oracle.D2Q37, 3, 24, 1.0
+    N = nx * ny
+    sim = make_sim(lat, (nx, ny, 1), tau, np.zeros((2, N)), bc=(0, 2, 0),
+                   T_lo=(1, 1.05, 1), T_hi=(1, 0.95, 1))
+    sim.init(np.ones(N), np.zeros((2, N)), np.ones(N))
+    sim.step(4000)
+    rho, u, T, q = sim.moments()
+    col = lambda v: v.reshape(ny, nx)[:, 0]
+    T, p, qy = col(T), col(rho * T), col(q[1])
+    bulk = slice(6, ny - 6)
+    assert np.max(np.abs(u.reshape(2, ny, nx)[:, bulk])) < 1e-6
+    assert np.max(np.abs(p[bulk] / p[bulk].mean() - 1)) < 1e-5
+    assert np.all(np.diff(T) < 0) and T[0] < 1.05 and T[-1] > 0.95
+    Tb = T[bulk]
+    slope = (Tb[-1] - Tb[0]) / (len(Tb) - 1)
+    assert np.max(np.abs(np.diff(Tb, 2))) < 1e-3 * abs(slope)
+    dTdy = slope / sim.c  # lattice spacing is c
+    lam = (2 + 2) / 2 * p[bulk].mean() * (tau - 0.5)
+    np.testing.assert_allclose(qy[bulk], -lam * dTdy, rtol=1e-2)
