@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the fused stream-collide step (one JSON line).
+
+Workload: thermal Rayleigh-Benard cell on D2Q37, 1024 x 512 sites, walls at
+y = -1/2 (T = 1.05) and y = 511.5 (T = 0.95), periodic in x, uniform gravity
+g_y = -1e-5, tau-hat = 0.6, populations stored as FP32 deviations f_i - w_i,
+seeded 1e-4 temperature perturbation (workloads.rayleigh_benard).
+
+One benchmark step = lbm_step(ctx, INNER) (INNER fused stream-collide
+launches) followed by lbm_conserved (the FP64 conservation / stability
+diagnostic), i.e. one pass over every row of the hot path.  L2 is flushed
+(256 MiB write) before every timed step, outside the timed interval.
+
+Multi-GPU (torchrun): every rank runs its own independent grid (weak scaling,
+no data-path collective); the timing is the max over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (one
+oracle LBM step over the same grid per benchmark step).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline, FP32-shifted vs FP64 at stated L2 error; serving p50/p99"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lattice_tables.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--inner", type=int, default=50, help="LBM steps per benchmark step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--nx", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=512)
+    return ap.parse_args()
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2302_04741_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        with open(path) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------- the oracle arm
+def oracle_rate(w, steps, warmup, budget_s=None):
+    """MLUPS of the FP64 CPU oracle on workload w (host cores)."""
+    import oracle
+    from paper_2302_04741_gb300 import workloads as W
+
+    oracle.set_threads(os.cpu_count() or 1)
+    g = W.g_field_array(w["lattice"], w["shape"], w["g"])
+    s = oracle.OracleSim(w["lattice"], *w["shape"], w["tau"], g, force_order=w["force_order"],
+                         bc=w["bc"], T_lo=w["T_lo"], T_hi=w["T_hi"])
+    s.init(w["rho"], w["u"], w["T"])
+    N = int(np.prod(w["shape"]))
+    s.step(warmup)
+    if budget_s is not None:
+        t0 = time.perf_counter()
+        s.step(1)
+        t1 = time.perf_counter() - t0
+        steps = int(max(1, min(steps, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(steps)
+    dt = time.perf_counter() - t0
+    return N * steps / dt / 1e6, steps, dt, oracle.get_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from paper_2302_04741_gb300 import workloads as W
+
+    w = W.rayleigh_benard(nx=args.nx, ny=args.ny, precision=W.FP64)
+    mlups, steps, dt, cores = oracle_rate(w, args.steps, args.warmup)
+    sample = f"FP64 oracle, full {args.nx}x{args.ny} D2Q37 Rayleigh-Benard grid, {steps} LBM steps"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"rayleigh_benard_d2q37_{args.nx}x{args.ny}", "lattice": "D2Q37",
+                   "grid": [args.nx, args.ny], "precision": "fp64 (oracle)", "bc": "thermal walls y, periodic x",
+                   "step": "one oracle LBM step over the full grid"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm
+def time_context(lbm, torch, sim, stream, flush, K, W_, inner):
+    """Times K benchmark steps (after W_ warm-up ones).  Returns total device
+    ms, summed ms of the step launches, and the launches counted."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for _ in range(W_):
+        sim.step(inner)
+        sim.conserved()
+    torch.cuda.synchronize()
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(inner)
+        ev[k][1].record(stream)
+        sim.conserved()
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    total = sum(e[0].elapsed_time(e[2]) for e in ev)
+    kern = sum(e[0].elapsed_time(e[1]) for e in ev)
+    return total, kern, K * (inner + 2)
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import paper_2302_04741_gb300 as lbm
+    from paper_2302_04741_gb300 import build as lbm_build
+    from paper_2302_04741_gb300 import workloads as W
+
+    if rank == 0 or world == 1:
+        lbm_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    lbm.lib()
+
+    nx, ny, inner, K, Wm = args.nx, args.ny, args.inner, args.steps, args.warmup
+    N = nx * ny
+    Q = 37
+    stream = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
+    w32 = W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP32_SHIFTED, seed=2 + rank)
+    sim = lbm.Sim(w32, stream=stream.cuda_stream).init()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, kern_ms, launches = time_context(lbm, torch, sim, stream, flush, K, Wm, inner)
+    barrier()
+    clk = clocks.stop()
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * N * inner * K / (t_max / 1e3) / 1e6
+
+    bytes_per_launch = 2 * Q * 4 * N
+    t_launch = kern_ms / 1e3 / (K * inner)
+    achieved = bytes_per_launch / t_launch / 1e9
+    peak, peak_kind = measured_peak()
+    traffic = profiled_traffic("k_step_fp32_rayleigh_benard_1024x512.md")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "kernel": "k_step<D2Q37, FP32_SHIFTED, order 2>",
+                "bytes_per_launch": bytes_per_launch, "avg_launch_us": t_launch * 1e6}
+
+    extra = {}
+    # FP64 storage, same workload (the FP32/FP64 ratio of the target)
+    if not args.no_fp64:
+        w64 = W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP64, seed=2 + rank)
+        sim64 = lbm.Sim(w64, stream=stream.cuda_stream).init()
+        K64 = max(2, min(K, 5))
+        t64, k64, _ = time_context(lbm, torch, sim64, stream, flush, K64, 1, inner)
+        v64 = N * inner * K64 / (t64 / 1e3) / 1e6
+        a64 = 2 * Q * 8 * N / (k64 / 1e3 / (K64 * inner)) / 1e9
+        extra["fp64"] = {"value": v64, "unit": "MLUPS", "roofline_frac_hbm": a64 / peak,
+                         "achieved_gbs": a64, "ratio_fp32_over_fp64": value / world / v64}
+        sim64.close()
+        # accuracy of the FP32-shifted state against the FP64 state, same steps
+        acc_steps = 1000
+        a = lbm.Sim(w32, stream=stream.cuda_stream).init()
+        b = lbm.Sim(w64, stream=stream.cuda_stream).init()
+        a.step(acc_steps)
+        b.step(acc_steps)
+        ma, mb = a.moments(), b.moments()
+        qf = 1e-3 * max(float(np.abs(mb[1]).max()), 1e-3) * math.sqrt(mb[1].size)
+        errs = {}
+        for nm, x, y in zip(("rho", "u", "T", "q"), ma, mb):
+            fl = qf if nm == "q" else 0.0
+            errs[nm] = float(np.linalg.norm(x - y) / max(np.linalg.norm(y), fl))
+        extra["l2_fp32_vs_fp64_gpu"] = {"steps": acc_steps, **errs}
+        a.close()
+        b.close()
+
+    # end to end: host arrays in, moments out, through the C ABI
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_in = [pin(w32["rho"]), pin(w32["u"]), pin(w32["T"])]
+    h_out = [torch.empty(N, dtype=torch.float64).pin_memory(),
+             torch.empty(2 * N, dtype=torch.float64).pin_memory(),
+             torch.empty(N, dtype=torch.float64).pin_memory(),
+             torch.empty(2 * N, dtype=torch.float64).pin_memory()]
+    e2e_sim = lbm.Sim(w32, stream=stream.cuda_stream)
+    Ke = max(3, K // 4)
+    lbm.lbm_init(e2e_sim.ctx, *h_in)
+    e2e_sim.step(inner)
+    lbm.lbm_moments(e2e_sim.ctx, *h_out)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        lbm.lbm_init(e2e_sim.ctx, *h_in)
+        e2e_sim.step(inner)
+        lbm.lbm_moments(e2e_sim.ctx, *h_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e = {"value": world * N * inner * Ke / (e2e_ms / 1e3) / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 4 * N * 8, "d2h_bytes_per_step": 6 * N * 8,
+           "step": f"lbm_init(pinned host rho,u,T) + lbm_step({inner}) + lbm_moments(pinned host)"}
+    e2e_sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mlups, steps, dt, cores = oracle_rate(W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP64),
+                                              40, 0, budget_s=12.0)
+        cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle, full {nx}x{ny} grid, {steps} LBM steps ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
+            "warmup": Wm, "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rayleigh_benard_d2q37_{nx}x{ny}", "lattice": "D2Q37",
+                       "grid": [nx, ny], "precision": "fp32_shifted", "tau_hat": 0.6,
+                       "g": [0.0, -1e-5], "walls": "thermal y (1.05 / 0.95), periodic x",
+                       "force_order": 2, "inner_lbm_steps_per_step": inner,
+                       "step": f"lbm_step({inner}) + lbm_conserved",
+                       "l2": "256 MiB flush before every timed step (outside the timed interval); "
+                             "working set 2 x 77.6 MB",
+                       "parallelism": f"{world} independent grids" if world > 1 else "1 grid"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) thermal compressible lattice
+ * Boltzmann library: one fused pull-stream / BGK-collide step with the
+ * Hermite-expanded body force of Li & Shan, "Body-force modelling in thermal
+ * compressible flows with lattice Boltzmann method" (arXiv 2302.04741).
+ *
+ * What one step computes (Sec. 2):
+ *   f~_i(x, t+1) = f*_i(x - e_i, t)                              (pull stream)
+ *   f*_i = f~_i - (f~_i - f0_i)/tau + (1 - 1/(2 tau)) F_i          (Eq. lbm)
+ * with f0_i the Hermite-expanded equilibrium (4th order on D2Q37, 3rd on
+ * D3Q39) and F_i the discrete body force up to the third moment (Eq. fi,
+ * without the deviatoric-stress terms), both evaluated at the mid-point
+ * state rho, u + g/2, theta; tau is the collision divisor tau-hat of Eq. lbm
+ * (tau-hat = tau + 1/2 in the paper's notation, so the kinematic viscosity is
+ * theta (tau - 1/2) in lattice units where the lattice spacing is c).
+ *
+ * Conventions for every entry point:
+ *   - Returns an lbm_status (0 = LBM_OK, negative = error); no exception
+ *     crosses the ABI.  lbm_last_error() gives the message of the last error
+ *     of a context.
+ *   - The library owns all device memory of a context (cudaMalloc at create,
+ *     cudaFree at destroy).  Caller arrays are only read or written during
+ *     the call; the caller keeps ownership.
+ *   - Array arguments may be host or device pointers (detected with
+ *     cudaPointerGetAttributes); device pointers must be on the context's
+ *     device.  Fields are row-major [nz][ny][nx], x fastest, N = nx*ny*nz
+ *     sites; vector fields are component-major: u[a*N + site].
+ *   - Velocities and accelerations are in units of sqrt(theta_0), theta_0 = 1
+ *     (the units in which the quadrature is exact); the lattice spacing is c
+ *     (lbm_lattice_info) and the time step is 1.
+ *   - All work is issued on the context's stream.  lbm_step returns without
+ *     synchronising; calls that hand results to the caller (lbm_moments,
+ *     lbm_conserved, lbm_get_*) synchronise that stream before returning.
+ *   - One context must not be used from two host threads at once; separate
+ *     contexts are independent.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Velocity sets (Sec. 3: D2Q37, ninth-order Gauss-Hermite rule with lattice
+ * constant c ~ 1.19698; D3Q39: seventh-order rule, c = sqrt(3/2)). */
+typedef enum { LBM_D2Q37 = 0, LBM_D3Q39 = 1 } lbm_lattice;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,    /* bad argument (message says which)                   */
+  LBM_ENOMEM = -2,    /* device or host allocation failed                    */
+  LBM_ECUDA = -3,     /* a CUDA runtime call failed (message has the code)   */
+  LBM_EUNSTABLE = -4, /* lbm_conserved found NaN/Inf or rho <= 0 or T <= 0   */
+  LBM_ETIMEOUT = -5,  /* a bounded device wait ran out                       */
+  LBM_ESTATE = -6,    /* call out of order (e.g. lbm_step before lbm_init)   */
+  LBM_EIO = -7        /* checkpoint file could not be read or written        */
+} lbm_status;
+
+/* Body-force acceleration g(x) (the g of Eq. BGK). */
+enum { LBM_G_UNIFORM = 0, /* g = g0                                             */
+       LBM_G_SINE = 1,    /* g = g0 * sin(2 pi x_a / n_a), a = wave_axis        */
+       LBM_G_FIELD = 2 }; /* g = field[a*N + site], D components, caller-owned,
+                             copied to the device at lbm_create                */
+typedef struct {
+  int kind;
+  double g0[3];
+  int wave_axis;
+  const double *field;
+} lbm_gfield;
+
+/* Population storage (the codec wraps the pull and the store of a step). */
+enum { LBM_FP64 = 0,         /* f_i in IEEE double, arithmetic in double          */
+       LBM_FP32_SHIFTED = 1, /* f_i - w_i rho0 (rho0 = 1) in float, arithmetic in float */
+       LBM_FP16_SCALED = 2 };/* half(s (f_i - w_i) / w_i), one scale s per grid chosen
+                                at lbm_init, arithmetic in float               */
+
+/* Boundary condition per axis.  Walls are allowed on the LAST axis only (y on
+ * D2Q37, z on D3Q39), at x_a = -1/2 and n_a - 1/2, and need n_a >= 6.  The
+ * paper's multi-speed boundary rule is unpublished (Sec. 3), so the library
+ * uses its own mass-conserving rules:
+ *   BOUNCE_BACK:  f~_i(x) = f*_{-i}(x') with x' the same column and the wall
+ *                 coordinate mirrored, x'_a = e_ia - 1 - x_a at the low wall
+ *                 (2 n_a - 1 - (x_a - e_ia) at the high wall);
+ *   THERMAL_WALL: diffuse reflection: those slots receive
+ *                 rho_w f0_i(1, 0, T_wall), rho_w chosen per column so that the
+ *                 column's incoming mass equals its outgoing mass. */
+enum { LBM_PERIODIC = 0, LBM_BOUNCE_BACK = 1, LBM_THERMAL_WALL = 2 };
+
+typedef struct {
+  int precision;     /* LBM_FP64 | LBM_FP32_SHIFTED | LBM_FP16_SCALED         */
+  int force_order;   /* the paper's N in Eq. F: force terms n <= N+1.
+                        0: n = 1 only; 1: n <= 2 (the Guo scheme, Sec. 2);
+                        2: n <= 3, the third-moment term of Eq. fi (default)  */
+  int include_sigma; /* deviatoric-stress terms of Eq. fi: must be 0 (the
+                        paper neglects them, Sec. 2 and 3.1)                 */
+  int bc[3];         /* per axis: LBM_PERIODIC | LBM_BOUNCE_BACK | LBM_THERMAL_WALL */
+  double T_lo[3];    /* wall temperature at x_a = -1/2 (THERMAL_WALL)         */
+  double T_hi[3];    /* wall temperature at x_a = n_a - 1/2                   */
+  void *stream;      /* cudaStream_t to issue work on; NULL = legacy default */
+  int block_x;       /* threads per block along x for the step kernel
+                        (0 = library default; multiple of 32, <= 256)        */
+  int graph_steps;   /* > 0: lbm_step replays a captured CUDA graph of this
+                        many steps (even); 0 = plain launches                */
+} lbm_options;
+
+/* Fills *opt with the defaults: FP64, force_order 2, no sigma, fully periodic,
+ * wall temperatures 1, NULL stream, library block shape, no graph. */
+void lbm_default_options(lbm_options *opt);
+
+/* Velocity set of a lattice: D, Q, c, the integer vectors e (Q*3, the
+ * library's direction order: rest first, then opposite pairs), the weights w
+ * (Q).  Any output pointer may be NULL.  Host pointers only. */
+int lbm_lattice_info(lbm_lattice lat, int *D, int *Q, double *c, int *e, double *w);
+
+/* Creates a context on the current CUDA device for an nx*ny*nz grid (nz must
+ * be 1 on D2Q37).  tau is the collision divisor tau-hat > 1/2.  g may be NULL
+ * (no force).  opt may be NULL (defaults).  Allocates two population buffers
+ * (ping-pong), the force table and reduction scratch.  *out receives the
+ * context, or NULL on error. */
+int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gfield *g,
+               const lbm_options *opt, lbm_ctx **out);
+
+/* Sets the state to the Maxwellian with the given density, velocity and
+ * temperature (the physical fields at t = 0): it stores
+ * f~_i = f0_i(rho, u, T) - F_i(rho, u, T)/2 (the auxiliary distribution of the
+ * second-order scheme, Sec. 2) at the slots the next pull reads, so that
+ * lbm_moments right after lbm_init returns the given fields (exactly up to
+ * round-off for periodic and bounce-back boundaries).  rho: N, u: D*N,
+ * T: N, doubles, host or device.  For LBM_FP16_SCALED this also fixes the
+ * grid's scale.  Resets the step counter. */
+int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *T);
+
+/* Advances n >= 0 steps (one fused pull-stream + collide launch per step, or
+ * graph replays).  Asynchronous on the context's stream. */
+int lbm_step(lbm_ctx *ctx, int n);
+
+/* Physical mid-point moments of the current state, in double: rho (N),
+ * u (D*N) = sum f~ xi / rho + g/2, T (N) = theta, and the heat flux q (D*N),
+ * q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2) |xi_i - u|^2 (xi_i - u)
+ * (the physical non-equilibrium part, Sec. 2).  Any output may be NULL.
+ * Host or device pointers.  Synchronises the stream. */
+int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *q);
+
+/* Global sums over the grid, in double with compensated (two-sum) block
+ * reductions in a fixed order (deterministic for a fixed grid): mass =
+ * sum rho, mom[D] = sum rho u, energy = sum rho (|u|^2 + D theta)/2, all
+ * physical mid-point values.  Any output may be NULL (host pointers).
+ * Returns LBM_EUNSTABLE if any site has a non-finite moment, rho <= 0 or
+ * theta <= 0 (the sums are still written).  Synchronises the stream. */
+int lbm_conserved(lbm_ctx *ctx, double *mass, double *mom, double *energy);
+
+/* The pulled (pre-collision) distribution f~ of the current state, decoded to
+ * double: out[i*N + site], Q*N values, library direction order. */
+int lbm_get_populations(lbm_ctx *ctx, double *out);
+
+/* The stored post-collision state f* decoded to double (Q*N), and its inverse
+ * (values are rounded to the storage precision).  With lbm_step(ctx, 1) these
+ * give one step of the method from an arbitrary state. */
+int lbm_get_state(lbm_ctx *ctx, double *out);
+int lbm_set_state(lbm_ctx *ctx, const double *in);
+
+/* Steps taken since lbm_init / lbm_load. */
+long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Scale s of the LBM_FP16_SCALED codec (0 for the other codecs). */
+double lbm_fp16_scale(const lbm_ctx *ctx);
+
+/* Checkpoint: writes / reads the raw population buffer, the codec scale, the
+ * step counter and the grid description.  lbm_load requires a context created
+ * with the same lattice, grid and precision; the continuation after a load is
+ * bitwise identical to the uninterrupted run. */
+int lbm_save(lbm_ctx *ctx, const char *path);
+int lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Device bytes held by a context. */
+size_t lbm_device_bytes(const lbm_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed lbm_create when
+ * ctx is NULL).  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Frees all device memory of the context and the context itself.  NULL is a
+ * no-op. */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

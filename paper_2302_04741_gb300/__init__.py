@@ -1,0 +1,299 @@
+"""GB300-native thermal compressible lattice Boltzmann step with the
+third-order Hermite body force of Li & Shan (arXiv 2302.04741).
+
+This package is a thin ctypes binding of the C ABI in ``include/lbm.h``
+(functions of the same names) plus ``Sim``, a convenience wrapper that only
+allocates output arrays and marshals arguments.  Every step of the method
+runs in the CUDA library ``_build/liblbm_gb300.so``; there is no CPU path:
+if the library is missing or cannot be loaded, every call raises.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); they are
+passed by pointer.  Device arrays must be contiguous float64 on the current
+device.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import workloads  # noqa: F401  (input generators, no method arithmetic)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbm_gb300.so")
+
+LBM_D2Q37, LBM_D3Q39 = 0, 1
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTATE, LBM_EIO = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+LBM_G_UNIFORM, LBM_G_SINE, LBM_G_FIELD = 0, 1, 2
+LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SCALED = 0, 1, 2
+LBM_PERIODIC, LBM_BOUNCE_BACK, LBM_THERMAL_WALL = 0, 1, 2
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
+                -4: "LBM_EUNSTABLE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_EIO"}
+
+
+class lbm_gfield(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("g0", ctypes.c_double * 3), ("wave_axis", ctypes.c_int),
+                ("field", ctypes.c_void_p)]
+
+
+class lbm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("force_order", ctypes.c_int),
+                ("include_sigma", ctypes.c_int), ("bc", ctypes.c_int * 3),
+                ("T_lo", ctypes.c_double * 3), ("T_hi", ctypes.c_double * 3),
+                ("stream", ctypes.c_void_p), ("block_x", ctypes.c_int),
+                ("graph_steps", ctypes.c_int)]
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_2302_04741_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        L.lbm_default_options.argtypes = [ctypes.POINTER(lbm_options)]
+        L.lbm_default_options.restype = None
+        L.lbm_lattice_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int), _dp,
+                                       ctypes.POINTER(ctypes.c_int), _dp]
+        L.lbm_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.POINTER(lbm_gfield),
+                                 ctypes.POINTER(lbm_options), ctypes.POINTER(_vp)]
+        for name in ("lbm_init",):
+            getattr(L, name).argtypes = [_vp, _vp, _vp, _vp]
+        L.lbm_step.argtypes = [_vp, ctypes.c_int]
+        L.lbm_moments.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.lbm_conserved.argtypes = [_vp, _dp, _dp, _dp]
+        for name in ("lbm_get_populations", "lbm_get_state", "lbm_set_state"):
+            getattr(L, name).argtypes = [_vp, _vp]
+        L.lbm_step_count.argtypes = [_vp]
+        L.lbm_step_count.restype = ctypes.c_longlong
+        L.lbm_fp16_scale.argtypes = [_vp]
+        L.lbm_fp16_scale.restype = ctypes.c_double
+        L.lbm_device_bytes.argtypes = [_vp]
+        L.lbm_device_bytes.restype = ctypes.c_size_t
+        L.lbm_save.argtypes = [_vp, ctypes.c_char_p]
+        L.lbm_load.argtypes = [_vp, ctypes.c_char_p]
+        L.lbm_last_error.argtypes = [_vp]
+        L.lbm_last_error.restype = ctypes.c_char_p
+        L.lbm_destroy.argtypes = [_vp]
+        L.lbm_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc, ctx=None):
+    if rc != LBM_OK:
+        raise LbmError(rc, lib().lbm_last_error(ctx).decode())
+    return rc
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (must be contiguous float64)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+            raise TypeError("torch tensors must be contiguous float64")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("numpy arrays must be C-contiguous float64")
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- the C ABI
+def lbm_default_options():
+    o = lbm_options()
+    lib().lbm_default_options(ctypes.byref(o))
+    return o
+
+
+def lbm_lattice_info(lat):
+    """(D, Q, c, e[Q, 3] int, w[Q]) in the library's direction order."""
+    D, Q = ctypes.c_int(), ctypes.c_int()
+    c = ctypes.c_double()
+    e = np.zeros((39, 3), dtype=np.int32)
+    w = np.zeros(39)
+    _check(lib().lbm_lattice_info(lat, ctypes.byref(D), ctypes.byref(Q), ctypes.byref(c),
+                                  e.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  w.ctypes.data_as(_dp)))
+    q = Q.value
+    return D.value, q, c.value, e[:q].copy(), w[:q].copy()
+
+
+def make_gfield(g):
+    """lbm_gfield from a workload descriptor dict (see workloads.g_field_array)."""
+    gf = lbm_gfield()
+    gf.kind = g["kind"]
+    g0 = list(g.get("g0", (0.0, 0.0, 0.0))) + [0.0] * 3
+    for a in range(3):
+        gf.g0[a] = g0[a]
+    gf.wave_axis = g.get("wave_axis", 0)
+    gf.field = _ptr(g["field"]) if g["kind"] == LBM_G_FIELD else None
+    return gf
+
+
+def lbm_create(lat, nx, ny, nz, tau, g=None, opt=None):
+    ctx = _vp()
+    gf = make_gfield(g) if isinstance(g, dict) else g
+    rc = lib().lbm_create(lat, nx, ny, nz, tau, ctypes.byref(gf) if gf is not None else None,
+                          ctypes.byref(opt) if opt is not None else None, ctypes.byref(ctx))
+    _check(rc)
+    return ctx
+
+
+def lbm_init(ctx, rho, u, T):
+    _check(lib().lbm_init(ctx, _ptr(rho), _ptr(u), _ptr(T)), ctx)
+
+
+def lbm_step(ctx, n):
+    _check(lib().lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_moments(ctx, rho=None, u=None, T=None, q=None):
+    _check(lib().lbm_moments(ctx, _ptr(rho), _ptr(u), _ptr(T), _ptr(q)), ctx)
+
+
+def lbm_conserved(ctx, D, raise_unstable=True):
+    """(status, mass, momentum[D], energy)."""
+    m, e = ctypes.c_double(), ctypes.c_double()
+    mom = (ctypes.c_double * 3)()
+    rc = lib().lbm_conserved(ctx, ctypes.byref(m), mom, ctypes.byref(e))
+    if rc != LBM_EUNSTABLE or raise_unstable:
+        _check(rc, ctx)
+    return rc, m.value, np.array(mom[:D]), e.value
+
+
+def lbm_get_populations(ctx, out):
+    _check(lib().lbm_get_populations(ctx, _ptr(out)), ctx)
+
+
+def lbm_get_state(ctx, out):
+    _check(lib().lbm_get_state(ctx, _ptr(out)), ctx)
+
+
+def lbm_set_state(ctx, inp):
+    _check(lib().lbm_set_state(ctx, _ptr(inp)), ctx)
+
+
+def lbm_step_count(ctx):
+    return int(lib().lbm_step_count(ctx))
+
+
+def lbm_fp16_scale(ctx):
+    return float(lib().lbm_fp16_scale(ctx))
+
+
+def lbm_device_bytes(ctx):
+    return int(lib().lbm_device_bytes(ctx))
+
+
+def lbm_save(ctx, path):
+    _check(lib().lbm_save(ctx, os.fsencode(path)), ctx)
+
+
+def lbm_load(ctx, path):
+    _check(lib().lbm_load(ctx, os.fsencode(path)), ctx)
+
+
+def lbm_last_error(ctx=None):
+    return lib().lbm_last_error(ctx).decode()
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        lib().lbm_destroy(ctx)
+
+
+# ------------------------------------------------------------ convenience
+def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
+            T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0):
+    o = lbm_default_options()
+    o.precision = precision
+    o.force_order = force_order
+    for a in range(3):
+        o.bc[a] = bc[a]
+        o.T_lo[a] = T_lo[a]
+        o.T_hi[a] = T_hi[a]
+    o.stream = stream
+    o.block_x = block_x
+    o.graph_steps = graph_steps
+    return o
+
+
+class Sim:
+    """One simulation context: create / init / step / moments / destroy.
+
+    ``w`` is a workload dict (see ``workloads``); ``stream`` an integer
+    cudaStream_t (e.g. ``torch.cuda.current_stream().cuda_stream``) or None.
+    """
+
+    def __init__(self, w, stream=None, block_x=0, graph_steps=0, precision=None):
+        self.w = w
+        self.lat = w["lattice"]
+        self.D, self.Q, self.c, self.e, self.wts = lbm_lattice_info(self.lat)
+        self.shape = w["shape"]
+        self.N = self.shape[0] * self.shape[1] * self.shape[2]
+        prec = w.get("precision", LBM_FP64) if precision is None else precision
+        self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
+                           w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
+                           block_x, graph_steps)
+        g = w.get("g")
+        self._gfield = g
+        self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def init(self, rho=None, u=None, T=None):
+        rho = self.w["rho"] if rho is None else rho
+        u = self.w["u"] if u is None else u
+        T = self.w["T"] if T is None else T
+        lbm_init(self.ctx, np.ascontiguousarray(rho, dtype=np.float64) if isinstance(rho, np.ndarray) else rho,
+                 np.ascontiguousarray(u, dtype=np.float64) if isinstance(u, np.ndarray) else u,
+                 np.ascontiguousarray(T, dtype=np.float64) if isinstance(T, np.ndarray) else T)
+        return self
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros((self.D, self.N))
+        T = np.zeros(self.N)
+        q = np.zeros((self.D, self.N))
+        lbm_moments(self.ctx, rho, u, T, q)
+        return rho, u, T, q
+
+    def conserved(self, raise_unstable=True):
+        return lbm_conserved(self.ctx, self.D, raise_unstable)
+
+    def populations(self):
+        out = np.zeros((self.Q, self.N))
+        lbm_get_populations(self.ctx, out)
+        return out
+
+    def get_state(self):
+        out = np.zeros((self.Q, self.N))
+        lbm_get_state(self.ctx, out)
+        return out
+
+    def set_state(self, f):
+        lbm_set_state(self.ctx, np.ascontiguousarray(f, dtype=np.float64))

@@ -1,0 +1,641 @@
+// lbm_abi.cu -- the C ABI declared in include/lbm.h: context management,
+// argument validation, device memory, launches on the context's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.cuh"
+
+using lbm::StepParams;
+
+struct lbm_ctx {
+  int lat = 0, D = 0, Q = 0, nx = 0, ny = 0, nz = 0;
+  int N = 0;
+  double tau = 0.0;
+  lbm_options opt{};
+  const lbm::LatticeOps* ops = nullptr;
+  size_t elem = 0;             // bytes per stored population value
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;                 // f[cur] holds the current post-collision state
+  double* gtab = nullptr;      // force table / field
+  double* part = nullptr;      // conservation partials (2 * NCONS per block)
+  unsigned* bad = nullptr;     // bad-site counts per block
+  double* dres = nullptr;      // final reduction result
+  unsigned* dmax = nullptr;    // FP16 init: max |d/w| bits
+  double* hres = nullptr;      // pinned host copy of the result
+  double* tmp = nullptr;       // (2 + 2D) * N doubles, lazily allocated
+  int nblk_cons = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  StepParams p{};
+  bool initialised = false;
+  long long steps = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  size_t bytes = 0;
+  int device = 0;
+  std::string err;
+};
+
+namespace {
+
+std::string g_create_error = "no error";
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define LBM_CUDA(ctx, call)                                                                   \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, LBM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                                        \
+  } while (0)
+
+const lbm::LatticeOps* ops_of(int lat) {
+  if (lat == LBM_D2Q37) return &lbm::ops_d2q37();
+  if (lat == LBM_D3Q39) return &lbm::ops_d3q39();
+  return nullptr;
+}
+
+template <class L>
+void info_of(int* D, int* Q, double* c, int* e, double* w) {
+  if (D) *D = L::D;
+  if (Q) *Q = L::Q;
+  if (c) *c = L::c;
+  for (int i = 0; i < L::Q; ++i) {
+    if (e)
+      for (int a = 0; a < 3; ++a) e[3 * i + a] = L::e[i][a];
+    if (w) w[i] = L::w[i];
+  }
+}
+
+// Equilibrium deviation f0_i(1, 0, T) - w_i = w_i A0(|xi_i|^2) of a wall at
+// rest (u = 0), the rest-frame value of the Hermite-expanded equilibrium.
+template <class L>
+void wall_equilibrium(double T, double* fwd, double* fw) {
+  const double th = T - 1.0;
+  const int D = L::D;
+  for (int i = 0; i < L::Q; ++i) {
+    const double e2 = L::e[i][0] * L::e[i][0] + L::e[i][1] * L::e[i][1] + L::e[i][2] * L::e[i][2];
+    const double X2 = L::c2 * e2;
+    double a0 = 0.5 * th * (X2 - D);
+    if (L::NEQ >= 4) a0 += (3.0 * th * th * (X2 * X2 - 2.0 * (D + 2) * X2 + D * (D + 2))) / 24.0;
+    fwd[i] = L::w[i] * a0;
+    fw[i] = L::w[i] + fwd[i];
+  }
+}
+
+template <class L>
+void wall_tables(StepParams& p, double T_lo, double T_hi) {
+  const int A = L::D - 1;
+  for (int side = 0; side < 2; ++side) {
+    wall_equilibrium<L>(side == 0 ? T_lo : T_hi, p.fwd[side], p.fw[side]);
+    double sfwd = 0.0, sfw = 0.0;
+    for (int i = 0; i < L::Q; ++i) {
+      const int eA = L::e[i][A];
+      const int cnt = side == 0 ? (eA > 0 ? eA : 0) : (eA < 0 ? -eA : 0);  // slots per column
+      sfwd += cnt * p.fwd[side][i];
+      sfw += cnt * p.fw[side][i];
+    }
+    p.wallA[side] = -sfwd;
+    p.wall_inv_den[side] = 1.0 / sfw;
+  }
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_tmp(lbm_ctx* c) {
+  if (c->tmp) return LBM_OK;
+  const size_t n = (size_t)(2 + 2 * c->D) * c->N;
+  if (cudaMalloc(&c->tmp, n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LBM_ENOMEM, "cannot allocate %zu bytes of moment buffers", n * sizeof(double));
+  }
+  c->bytes += n * sizeof(double);
+  return LBM_OK;
+}
+
+void drop_graphs(lbm_ctx* c) {
+  for (auto& g : c->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int launch_one_step(lbm_ctx* c) {
+  cudaError_t e = c->ops->step(c->opt.precision, c->opt.force_order, c->f[c->cur],
+                               c->f[c->cur ^ 1], c->p, c->opt.block_x, c->stream);
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
+  c->cur ^= 1;
+  return LBM_OK;
+}
+
+// Graph of graph_steps steps starting from buffer parity `par` (even length,
+// so the parity is restored).
+int build_graph(lbm_ctx* c, int par) {
+  cudaGraph_t g = nullptr;
+  const int saved = c->cur;
+  c->cur = par;
+  LBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LBM_OK;
+  for (int k = 0; k < c->opt.graph_steps && rc == LBM_OK; ++k) rc = launch_one_step(c);
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  c->cur = saved;
+  if (rc != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->graph[par], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_options(lbm_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = LBM_FP64;
+  o->force_order = 2;
+  o->include_sigma = 0;
+  for (int a = 0; a < 3; ++a) {
+    o->bc[a] = LBM_PERIODIC;
+    o->T_lo[a] = 1.0;
+    o->T_hi[a] = 1.0;
+  }
+  o->stream = nullptr;
+  o->block_x = 0;
+  o->graph_steps = 0;
+}
+
+int lbm_lattice_info(lbm_lattice lat, int* D, int* Q, double* c, int* e, double* w) {
+  if (lat == LBM_D2Q37) info_of<lbm::D2Q37>(D, Q, c, e, w);
+  else if (lat == LBM_D3Q39) info_of<lbm::D3Q39>(D, Q, c, e, w);
+  else return fail(nullptr, LBM_EINVAL, "unknown lattice %d", (int)lat);
+  return LBM_OK;
+}
+
+int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gfield* g,
+               const lbm_options* opt, lbm_ctx** out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  const lbm::LatticeOps* ops = ops_of(lat);
+  if (!ops) return fail(nullptr, LBM_EINVAL, "unknown lattice %d", (int)lat);
+  lbm_options o;
+  if (opt) o = *opt;
+  else lbm_default_options(&o);
+  const int D = ops->D;
+  if (D == 2 && nz != 1) return fail(nullptr, LBM_EINVAL, "D2Q37 needs nz == 1 (got %d)", nz);
+  if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "grid %dx%dx%d is empty", nx, ny, nz);
+  const long long N = (long long)nx * ny * nz;
+  if (N >= (1LL << 31)) return fail(nullptr, LBM_EINVAL, "grid has %lld >= 2^31 sites", N);
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau-hat must be > 1/2 (got %g)", tau);
+  if (o.precision < LBM_FP64 || o.precision > LBM_FP16_SCALED)
+    return fail(nullptr, LBM_EINVAL, "unknown precision %d", o.precision);
+  if (o.force_order < 0 || o.force_order > 2)
+    return fail(nullptr, LBM_EINVAL, "force_order must be 0, 1 or 2 (got %d)", o.force_order);
+  if (o.include_sigma) return fail(nullptr, LBM_EINVAL, "include_sigma is not supported");
+  const int n[3] = {nx, ny, nz};
+  int wall = lbm::W_NONE;
+  for (int a = 0; a < 3; ++a) {
+    const int b = a < D ? o.bc[a] : LBM_PERIODIC;
+    if (b < LBM_PERIODIC || b > LBM_THERMAL_WALL) return fail(nullptr, LBM_EINVAL, "bad bc[%d] = %d", a, b);
+    if (b != LBM_PERIODIC) {
+      if (a != D - 1) return fail(nullptr, LBM_EINVAL, "walls are supported on the last axis only (axis %d)", D - 1);
+      if (n[a] < 6) return fail(nullptr, LBM_EINVAL, "a walled axis needs >= 6 sites (got %d)", n[a]);
+      wall = b == LBM_BOUNCE_BACK ? lbm::W_BOUNCE : lbm::W_THERMAL;
+    } else if (a < D && n[a] < 3) {
+      return fail(nullptr, LBM_EINVAL, "a periodic axis needs >= 3 sites (axis %d has %d)", a, n[a]);
+    }
+  }
+  if (o.block_x == 0) o.block_x = 128;
+  if (o.block_x < 32 || o.block_x > 256 || o.block_x % 32)
+    return fail(nullptr, LBM_EINVAL, "block_x must be a multiple of 32 in [32, 256] (got %d)", o.block_x);
+  if (o.graph_steps < 0 || o.graph_steps % 2)
+    return fail(nullptr, LBM_EINVAL, "graph_steps must be even and >= 0 (got %d)", o.graph_steps);
+  lbm_gfield gf{};
+  gf.kind = LBM_G_UNIFORM;
+  if (g) gf = *g;
+  if (gf.kind < LBM_G_UNIFORM || gf.kind > LBM_G_FIELD) return fail(nullptr, LBM_EINVAL, "bad force kind %d", gf.kind);
+  if (gf.kind == LBM_G_SINE && (gf.wave_axis < 0 || gf.wave_axis >= D))
+    return fail(nullptr, LBM_EINVAL, "bad wave_axis %d", gf.wave_axis);
+  if (gf.kind == LBM_G_FIELD && !gf.field) return fail(nullptr, LBM_EINVAL, "force field is NULL");
+
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(nullptr, LBM_ENOMEM, "out of host memory");
+  c->lat = lat; c->D = D; c->Q = ops->Q; c->nx = nx; c->ny = ny; c->nz = nz; c->N = (int)N;
+  c->tau = tau; c->opt = o; c->ops = ops;
+  c->elem = o.precision == LBM_FP64 ? 8 : (o.precision == LBM_FP32_SHIFTED ? 4 : 2);
+  cudaGetDevice(&c->device);
+  auto bail = [&](int rc) {
+    const std::string msg = c->err;
+    lbm_destroy(c);
+    g_create_error = msg;
+    return rc;
+  };
+  if (o.stream) {
+    c->stream = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      fail(c, LBM_ECUDA, "cudaStreamCreate failed");
+      return bail(LBM_ECUDA);
+    }
+    c->own_stream = true;
+  }
+  const size_t fbytes = (size_t)c->Q * N * c->elem;
+  for (int k = 0; k < 2; ++k) {
+    if (cudaMalloc(&c->f[k], fbytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(c, LBM_ENOMEM, "cannot allocate %zu bytes of populations", fbytes);
+      return bail(LBM_ENOMEM);
+    }
+    c->bytes += fbytes;
+  }
+  // parameters
+  StepParams& p = c->p;
+  p.nx = nx; p.ny = ny; p.nz = nz; p.N = (int)N; p.wall = wall;
+  p.omega = 1.0 / tau;
+  p.gkind = gf.kind; p.gaxis = gf.wave_axis;
+  for (int a = 0; a < 3; ++a) p.g0[a] = a < D ? gf.g0[a] : 0.0;
+  p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
+  if (wall != lbm::W_NONE) {
+    if (lat == LBM_D2Q37) wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
+    else wall_tables<lbm::D3Q39>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
+  }
+  if (gf.kind == LBM_G_SINE) {
+    const int na = n[gf.wave_axis];
+    double* h = (double*)std::malloc(sizeof(double) * na);
+    if (!h) { fail(c, LBM_ENOMEM, "out of host memory"); return bail(LBM_ENOMEM); }
+    for (int k = 0; k < na; ++k) h[k] = std::sin(2.0 * M_PI * k / na);
+    cudaError_t e = cudaMalloc(&c->gtab, sizeof(double) * na);
+    if (e == cudaSuccess) e = cudaMemcpy(c->gtab, h, sizeof(double) * na, cudaMemcpyHostToDevice);
+    std::free(h);
+    if (e != cudaSuccess) { cudaGetLastError(); fail(c, LBM_ECUDA, "force table upload failed"); return bail(LBM_ECUDA); }
+    c->bytes += sizeof(double) * na;
+  } else if (gf.kind == LBM_G_FIELD) {
+    const size_t gb = sizeof(double) * D * N;
+    cudaError_t e = cudaMalloc(&c->gtab, gb);
+    if (e == cudaSuccess) e = cudaMemcpy(c->gtab, gf.field, gb, cudaMemcpyDefault);
+    if (e != cudaSuccess) { cudaGetLastError(); fail(c, LBM_ECUDA, "force field upload failed"); return bail(LBM_ECUDA); }
+    c->bytes += gb;
+  }
+  p.gtab = c->gtab;
+  // reduction scratch
+  c->nblk_cons = ((nx + 127) / 128) * ny * nz;
+  const size_t pb = sizeof(double) * 2 * lbm::NCONS * c->nblk_cons;
+  if (cudaMalloc(&c->part, pb) != cudaSuccess || cudaMalloc(&c->bad, sizeof(unsigned) * c->nblk_cons) != cudaSuccess ||
+      cudaMalloc(&c->dres, sizeof(double) * (2 * lbm::NCONS + 1)) != cudaSuccess ||
+      cudaMalloc(&c->dmax, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&c->hres, sizeof(double) * (2 * lbm::NCONS + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, LBM_ENOMEM, "cannot allocate reduction scratch");
+    return bail(LBM_ENOMEM);
+  }
+  c->bytes += pb + sizeof(unsigned) * c->nblk_cons + sizeof(double) * (2 * lbm::NCONS + 1) + sizeof(unsigned);
+  *out = c;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!rho || !u || !T) return fail(c, LBM_EINVAL, "rho, u and T are required");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const size_t N = (size_t)c->N;
+  const double *drho = rho, *du = u, *dT = T;
+  const bool dev = is_device_ptr(rho) && is_device_ptr(u) && is_device_ptr(T);
+  if (!dev) {
+    int rc = ensure_tmp(c);
+    if (rc) return rc;
+    double* t = c->tmp;
+    LBM_CUDA(c, cudaMemcpyAsync(t, rho, N * sizeof(double), cudaMemcpyDefault, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(t + N, u, c->D * N * sizeof(double), cudaMemcpyDefault, c->stream));
+    LBM_CUDA(c, cudaMemcpyAsync(t + (1 + c->D) * N, T, N * sizeof(double), cudaMemcpyDefault, c->stream));
+    drho = t; du = t + N; dT = t + (1 + c->D) * N;
+  }
+  drop_graphs(c);
+  c->cur = 0;
+  if (c->opt.precision == LBM_FP16_SCALED) {
+    LBM_CUDA(c, cudaMemsetAsync(c->dmax, 0, sizeof(unsigned), c->stream));
+    LBM_CUDA(c, c->ops->init(c->opt.precision, 0, drho, du, dT, c->f[0], c->dmax, c->opt.force_order, c->p, c->stream));
+    unsigned bits = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(&bits, c->dmax, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    float mx;
+    std::memcpy(&mx, &bits, sizeof mx);
+    if (!std::isfinite(mx)) return fail(c, LBM_EINVAL, "initial state is not finite");
+    // scale s = 2^k with max |d/w| * s in [2^12, 2^13): headroom of 8x below the
+    // half-precision maximum for the state to grow into
+    int k = 0;
+    if (mx > 0.f) k = 12 - (int)std::floor(std::log2((double)mx));
+    if (k > 60) k = 60;
+    if (k < -60) k = -60;
+    c->p.h_scale = std::ldexp(1.0f, k);
+    c->p.h_inv_scale = std::ldexp(1.0f, -k);
+  }
+  LBM_CUDA(c, c->ops->init(c->opt.precision, 1, drho, du, dT, c->f[0], nullptr, c->opt.force_order, c->p, c->stream));
+  if (!dev) LBM_CUDA(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed after return
+  c->initialised = true;
+  c->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0 (got %d)", n);
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  int left = n;
+  const int G = c->opt.graph_steps;
+  while (G > 0 && left >= G) {
+    if (!c->graph[c->cur]) {
+      int rc = build_graph(c, c->cur);
+      if (rc) return rc;
+    }
+    LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+    left -= G;
+  }
+  for (; left > 0; --left) {
+    int rc = launch_one_step(c);
+    if (rc) return rc;
+  }
+  c->steps += n;
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* c, double* rho, double* u, double* T, double* q) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_moments before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  int rc = ensure_tmp(c);
+  if (rc) return rc;
+  const size_t N = (size_t)c->N;
+  double* outs[4] = {rho, u, T, q};
+  const size_t cnt[4] = {N, c->D * N, N, c->D * N};
+  double* dst[4];
+  double* t = c->tmp;
+  for (int k = 0; k < 4; ++k) {
+    dst[k] = nullptr;
+    if (outs[k]) dst[k] = is_device_ptr(outs[k]) ? outs[k] : t;
+    t += cnt[k];
+  }
+  LBM_CUDA(c, c->ops->moments(c->opt.precision, c->f[c->cur], dst[0], dst[1], dst[2], dst[3],
+                              c->opt.force_order, c->p, c->stream));
+  for (int k = 0; k < 4; ++k)
+    if (outs[k] && dst[k] != outs[k])
+      LBM_CUDA(c, cudaMemcpyAsync(outs[k], dst[k], cnt[k] * sizeof(double), cudaMemcpyDefault, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_conserved(lbm_ctx* c, double* mass, double* mom, double* energy) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_conserved before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  LBM_CUDA(c, c->ops->conserved(c->opt.precision, c->f[c->cur], c->part, c->bad, c->p, c->stream));
+  lbm::k_conserved_final<<<1, 256, 0, c->stream>>>(c->part, c->bad, c->nblk_cons, c->dres);
+  LBM_CUDA(c, cudaGetLastError());
+  LBM_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * (2 * lbm::NCONS + 1), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double* r = c->hres;
+  if (mass) *mass = r[0] + r[1];
+  if (mom)
+    for (int a = 0; a < c->D; ++a) mom[a] = r[2 * (1 + a)] + r[2 * (1 + a) + 1];
+  if (energy) *energy = r[8] + r[9];
+  if (r[2 * lbm::NCONS] > 0.0)
+    return fail(c, LBM_EUNSTABLE, "%.0f sites have a non-finite moment, rho <= 0 or T <= 0",
+                r[2 * lbm::NCONS]);
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_ctx* c, double* out) {
+  if (!c || !out) return fail(c, LBM_EINVAL, "ctx and out are required");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_populations before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const size_t n = (size_t)c->Q * c->N;
+  const bool dev = is_device_ptr(out);
+  double* dst = out;
+  if (!dev) {
+    LBM_CUDA(c, cudaMallocAsync(&dst, n * sizeof(double), c->stream));
+  }
+  cudaError_t e = c->ops->pulled(c->opt.precision, c->f[c->cur], dst, c->p, c->stream);
+  if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (!dev) cudaFreeAsync(dst, c->stream);
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "get_populations failed: %s", cudaGetErrorString(e));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+static int state_io(lbm_ctx* c, double* io, int dir) {
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const size_t n = (size_t)c->Q * c->N;
+  const bool dev = is_device_ptr(io);
+  double* d = io;
+  if (!dev) {
+    LBM_CUDA(c, cudaMallocAsync(&d, n * sizeof(double), c->stream));
+    if (dir == 1) LBM_CUDA(c, cudaMemcpyAsync(d, io, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  cudaError_t e = c->ops->state(c->opt.precision, dir, c->f[c->cur], d, c->p, c->stream);
+  if (e == cudaSuccess && !dev && dir == 0)
+    e = cudaMemcpyAsync(io, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (!dev) cudaFreeAsync(d, c->stream);
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "state transfer failed: %s", cudaGetErrorString(e));
+  LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_get_state(lbm_ctx* c, double* out) {
+  if (!c || !out) return fail(c, LBM_EINVAL, "ctx and out are required");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_state before lbm_init");
+  return state_io(c, out, 0);
+}
+
+int lbm_set_state(lbm_ctx* c, const double* in) {
+  if (!c || !in) return fail(c, LBM_EINVAL, "ctx and in are required");
+  if (c->opt.precision == LBM_FP16_SCALED && !c->initialised)
+    return fail(c, LBM_ESTATE, "the FP16 scale is fixed by lbm_init; call it first");
+  drop_graphs(c);
+  int rc = state_io(c, const_cast<double*>(in), 1);
+  if (rc == LBM_OK) c->initialised = true;
+  return rc;
+}
+
+long long lbm_step_count(const lbm_ctx* c) { return c ? c->steps : 0; }
+
+double lbm_fp16_scale(const lbm_ctx* c) {
+  return (c && c->opt.precision == LBM_FP16_SCALED) ? (double)c->p.h_scale : 0.0;
+}
+
+size_t lbm_device_bytes(const lbm_ctx* c) { return c ? c->bytes : 0; }
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int version, lat, nx, ny, nz, precision;
+  float h_scale, h_inv_scale;
+  long long steps;
+  double tau;
+};
+}  // namespace
+
+int lbm_save(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, LBM_EINVAL, "ctx and path are required");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "nothing to save before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const size_t nb = (size_t)c->Q * c->N * c->elem;
+  void* h = std::malloc(nb);
+  if (!h) return fail(c, LBM_ENOMEM, "out of host memory");
+  cudaError_t e = cudaMemcpyAsync(h, c->f[c->cur], nb, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    std::free(h);
+    return fail(c, LBM_ECUDA, "checkpoint copy failed: %s", cudaGetErrorString(e));
+  }
+  CkptHeader hd{};
+  std::memcpy(hd.magic, "LBMGB300", 8);
+  hd.version = 1; hd.lat = c->lat; hd.nx = c->nx; hd.ny = c->ny; hd.nz = c->nz;
+  hd.precision = c->opt.precision; hd.h_scale = c->p.h_scale; hd.h_inv_scale = c->p.h_inv_scale;
+  hd.steps = c->steps; hd.tau = c->tau;
+  FILE* fp = std::fopen(path, "wb");
+  bool ok = fp && std::fwrite(&hd, sizeof hd, 1, fp) == 1 && std::fwrite(h, 1, nb, fp) == nb;
+  if (fp) ok = (std::fclose(fp) == 0) && ok;
+  std::free(h);
+  if (!ok) return fail(c, LBM_EIO, "cannot write checkpoint %s", path);
+  return LBM_OK;
+}
+
+int lbm_load(lbm_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, LBM_EINVAL, "ctx and path are required");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(c, LBM_EIO, "cannot open checkpoint %s", path);
+  CkptHeader hd{};
+  if (std::fread(&hd, sizeof hd, 1, fp) != 1 || std::memcmp(hd.magic, "LBMGB300", 8) || hd.version != 1) {
+    std::fclose(fp);
+    return fail(c, LBM_EIO, "%s is not a checkpoint of this library", path);
+  }
+  if (hd.lat != c->lat || hd.nx != c->nx || hd.ny != c->ny || hd.nz != c->nz || hd.precision != c->opt.precision) {
+    std::fclose(fp);
+    return fail(c, LBM_EINVAL, "checkpoint grid/lattice/precision differ from the context");
+  }
+  const size_t nb = (size_t)c->Q * c->N * c->elem;
+  void* h = std::malloc(nb);
+  if (!h) {
+    std::fclose(fp);
+    return fail(c, LBM_ENOMEM, "out of host memory");
+  }
+  const bool ok = std::fread(h, 1, nb, fp) == nb;
+  std::fclose(fp);
+  if (!ok) {
+    std::free(h);
+    return fail(c, LBM_EIO, "checkpoint %s is truncated", path);
+  }
+  drop_graphs(c);
+  c->cur = 0;
+  cudaError_t e = cudaMemcpyAsync(c->f[0], h, nb, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  std::free(h);
+  if (e != cudaSuccess) return fail(c, LBM_ECUDA, "checkpoint upload failed: %s", cudaGetErrorString(e));
+  c->p.h_scale = hd.h_scale;
+  c->p.h_inv_scale = hd.h_inv_scale;
+  c->steps = hd.steps;
+  c->initialised = true;
+  return LBM_OK;
+}
+
+const char* lbm_last_error(const lbm_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.empty() ? "no error" : c->err.c_str();
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  cudaFree(c->f[0]);
+  cudaFree(c->f[1]);
+  cudaFree(c->gtab);
+  cudaFree(c->part);
+  cudaFree(c->bad);
+  cudaFree(c->dres);
+  cudaFree(c->dmax);
+  cudaFree(c->tmp);
+  if (c->hres) cudaFreeHost(c->hres);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  cudaGetLastError();
+  delete c;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------ final conservation pass
+namespace lbm {
+__global__ void __launch_bounds__(256) k_conserved_final(const double* __restrict__ part,
+                                                         const unsigned* __restrict__ badcount,
+                                                         int nblocks, double* __restrict__ out) {
+  __shared__ double sh_s[256][NCONS], sh_c[256][NCONS];
+  __shared__ unsigned sh_b[256];
+  KSum acc[NCONS];
+  for (int k = 0; k < NCONS; ++k) acc[k] = KSum{0.0, 0.0};
+  unsigned b = 0;
+  for (int blk = threadIdx.x; blk < nblocks; blk += 256) {
+    for (int k = 0; k < NCONS; ++k)
+      acc[k] = ksum_merge(acc[k], KSum{part[(size_t)blk * 2 * NCONS + 2 * k],
+                                       part[(size_t)blk * 2 * NCONS + 2 * k + 1]});
+    b += badcount[blk];
+  }
+  for (int k = 0; k < NCONS; ++k) {
+    sh_s[threadIdx.x][k] = acc[k].s;
+    sh_c[threadIdx.x][k] = acc[k].c;
+  }
+  sh_b[threadIdx.x] = b;
+  __syncthreads();
+  for (int half = 128; half > 0; half >>= 1) {
+    if (threadIdx.x < half) {
+      for (int k = 0; k < NCONS; ++k) {
+        KSum r = ksum_merge(KSum{sh_s[threadIdx.x][k], sh_c[threadIdx.x][k]},
+                            KSum{sh_s[threadIdx.x + half][k], sh_c[threadIdx.x + half][k]});
+        sh_s[threadIdx.x][k] = r.s;
+        sh_c[threadIdx.x][k] = r.c;
+      }
+      sh_b[threadIdx.x] += sh_b[threadIdx.x + half];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NCONS; ++k) {
+      out[2 * k] = sh_s[0][k];
+      out[2 * k + 1] = sh_c[0][k];
+    }
+    out[2 * NCONS] = (double)sh_b[0];
+  }
+}
+}  // namespace lbm

@@ -1,0 +1,345 @@
+// lbm_device.cuh -- device-side building blocks of the fused step.
+//
+// Notation follows Li & Shan (arXiv 2302.04741), Sec. 2: xi_i = c e_i are the
+// abscissae, w_i the weights, f~ the pulled (pre-collision) distribution, the
+// mid-point state is rho, u = u~ + g/2, theta.  All arithmetic works on the
+// deviations d_i = f~_i - w_i (rho_0 = 1), which keeps float arithmetic
+// accurate: the moments of the uniform state (sum w = 1, sum w xi = 0,
+// sum w xi^2 = D) are carried exactly and only the deviations are rounded.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lattice_tables.cuh"
+
+namespace lbm {
+
+constexpr int QMAX = 39;
+
+enum Precision { P_FP64 = 0, P_FP32S = 1, P_FP16S = 2 };
+enum Wall { W_NONE = 0, W_BOUNCE = 1, W_THERMAL = 2 };
+enum GKind { G_UNIFORM = 0, G_SINE = 1, G_FIELD = 2 };
+
+// Everything a step kernel needs, passed by value (constant bank).
+struct StepParams {
+  int nx, ny, nz;    // nz = 1 on D2Q37
+  int N;             // sites (< 2^31)
+  int wall;          // Wall, on the last axis (y for D = 2, z for D = 3)
+  double omega;      // 1 / tau-hat
+  int gkind;         // GKind
+  int gaxis;         // G_SINE: axis of the wave
+  double g0[3];      // G_UNIFORM / G_SINE amplitude
+  const double* gtab;  // G_SINE: sin(2 pi k / n_axis), k < n_axis; G_FIELD: D*N field
+  // thermal wall, side s = 0 (low) / 1 (high): fw = f0_i(1, 0, T_s), fwd = fw - w,
+  // wallA = -sum over one column's incoming slots of fwd, wall_inv_den = 1 / sum of fw
+  double fw[2][QMAX];
+  double fwd[2][QMAX];
+  double wallA[2];
+  double wall_inv_den[2];
+  float h_scale;      // FP16 codec scale s and 1/s
+  float h_inv_scale;
+};
+
+// ---------------------------------------------------------------- helpers
+// Compile-time index usable in device code (std::integral_constant's
+// conversion operator is host-only).
+template <int V>
+struct ic {
+  static constexpr int value = V;
+  __host__ __device__ constexpr operator int() const { return V; }
+};
+
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(ic<B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// acc + K * v for a compile-time integer K, without a multiply for K in {0, +-1}.
+template <int K, class R>
+__device__ __forceinline__ R mac(R v, R acc) {
+  if constexpr (K == 0) return acc;
+  else if constexpr (K == 1) return acc + v;
+  else if constexpr (K == -1) return acc - v;
+  else return fma(R(K), v, acc);
+}
+
+// K * v for a compile-time integer K.
+template <int K, class R>
+__device__ __forceinline__ R imul(R v) {
+  if constexpr (K == 0) return R(0);
+  else if constexpr (K == 1) return v;
+  else if constexpr (K == -1) return -v;
+  else return R(K) * v;
+}
+
+// Products by the quadrature constants (w_i, c, c^2, |xi|^2).  In float the
+// constant is carried as hi + lo (both floats, ~48 bits): a float-rounded
+// constant would break the identities sum w = 1, c^2 sum w e e = delta by
+// ~1e-7 and the collision would then create momentum and energy at that
+// relative rate every step.  In double the constant is used as is.
+struct F2 {
+  float hi, lo;
+};
+__host__ __device__ constexpr F2 f2_of(double k) {
+  return F2{float(k), float(k - double(float(k)))};
+}
+template <class R>
+__device__ __forceinline__ R kmul(double k, F2 k2, R x);
+template <>
+__device__ __forceinline__ float kmul<float>(double, F2 k2, float x) {
+  return fmaf(k2.hi, x, k2.lo * x);
+}
+template <>
+__device__ __forceinline__ double kmul<double>(double k, F2, double x) {
+  return k * x;
+}
+template <class L, int I, class R>
+__device__ __forceinline__ R mul_w(R x) {
+  constexpr double k = L::W(I);
+  constexpr F2 k2 = f2_of(k);
+  return kmul<R>(k, k2, x);
+}
+template <class L, class R>
+__device__ __forceinline__ R mul_c(R x) {
+  constexpr F2 k2 = f2_of(L::c);
+  return kmul<R>(L::c, k2, x);
+}
+template <class L, class R>
+__device__ __forceinline__ R mul_c2(R x) {
+  constexpr F2 k2 = f2_of(L::c2);
+  return kmul<R>(L::c2, k2, x);
+}
+
+// e_i . v for compile-time e_i.
+template <class L, int I, class R>
+__device__ __forceinline__ R edot(const R (&v)[3]) {
+  constexpr int ex = L::E(I, 0), ey = L::E(I, 1), ez = L::E(I, 2);
+  R acc = imul<ex>(v[0]);
+  acc = mac<ey>(v[1], acc);
+  if constexpr (L::D == 3) acc = mac<ez>(v[2], acc);
+  return acc;
+}
+
+// ------------------------------------------------------- storage codecs
+// decode(stored, i) -> deviation d_i = f_i - w_i ; encode(d_i, i) -> stored
+template <int P> struct Codec;
+
+template <> struct Codec<P_FP64> {
+  using T = double;
+  using R = double;
+  template <class L, int I>
+  __device__ __forceinline__ static R decode(T v, const StepParams&) { return v - L::W(I); }
+  template <class L, int I>
+  __device__ __forceinline__ static T encode(R d, const StepParams&) { return d + L::W(I); }
+  __device__ __forceinline__ static T load(const T* p) { return __ldg(p); }
+};
+
+template <> struct Codec<P_FP32S> {
+  using T = float;
+  using R = float;
+  template <class L, int I>
+  __device__ __forceinline__ static R decode(T v, const StepParams&) { return v; }
+  template <class L, int I>
+  __device__ __forceinline__ static T encode(R d, const StepParams&) { return d; }
+  __device__ __forceinline__ static T load(const T* p) { return __ldg(p); }
+};
+
+template <> struct Codec<P_FP16S> {
+  using T = __half;
+  using R = float;
+  template <class L, int I>
+  __device__ __forceinline__ static R decode(T v, const StepParams& p) {
+    constexpr float w = float(L::W(I));
+    return __half2float(v) * (w * p.h_inv_scale);
+  }
+  template <class L, int I>
+  __device__ __forceinline__ static T encode(R d, const StepParams& p) {
+    constexpr float iw = float(1.0 / L::W(I));
+    return __float2half_rn(d * (iw * p.h_scale));
+  }
+  __device__ __forceinline__ static T load(const T* p) { return __ldg(p); }
+};
+
+// ------------------------------------------------------------ body force
+template <class R>
+__device__ __forceinline__ void body_force(const StepParams& p, int x, int y, int z, int site,
+                                           R (&g)[3]) {
+  if (p.gkind == G_UNIFORM) {
+    g[0] = R(p.g0[0]); g[1] = R(p.g0[1]); g[2] = R(p.g0[2]);
+  } else if (p.gkind == G_SINE) {
+    const int k = p.gaxis == 0 ? x : (p.gaxis == 1 ? y : z);
+    const double s = __ldg(p.gtab + k);
+    g[0] = R(p.g0[0] * s); g[1] = R(p.g0[1] * s); g[2] = R(p.g0[2] * s);
+  } else {
+    g[0] = R(__ldg(p.gtab + site));
+    g[1] = R(__ldg(p.gtab + (size_t)p.N + site));
+    g[2] = p.nz > 1 ? R(__ldg(p.gtab + 2 * (size_t)p.N + site)) : R(0);
+  }
+}
+
+// --------------------------------------------------------- mid-point state
+// Moments of the pulled f~ (Eq. rut1) and the mid-point state of Eq. lbm:
+// rho, u = u~ + g/2 and the physical temperature
+// theta = (sum f~ xi^2 / rho - |u~|^2) / D + |g|^2 / (4 D).
+// Per shell (|xi|^2 = X2) it also prepares the coefficients of the
+// equilibrium polynomial p(t) = f0_i/(w_i rho) - 1 in t = xi_i . u:
+//   p = A0 + A1 t + A2 t^2 + t^3/6 + [NEQ = 4] t^4/24, with
+//   A0 = -u^2/2 + Th (X2 - D)/2
+//        + [NEQ=4] (3 u^4 - 6 Th u^2 (X2-D-2) + 3 Th^2 (X2^2 - 2(D+2) X2 + D(D+2)))/24
+//   A1 = 1 - u^2/2 + Th (X2 - D - 2)/2
+//   A2 = 1/2 + [NEQ=4] (-u^2 + Th (X2 - D - 4))/4,        Th = theta - 1,
+// i.e. sum_n a^(n)_0 : H^(n)(xi) / n! of Eq. fN with the Maxwellian
+// coefficients (Eq. f2 and its higher-order analogues) written out in t.
+// The force polynomial F_i/(w_i rho) (Eq. fi without sigma terms) is, with
+// s = xi_i . g and Z = -u^2 + Th (X2 - D - 2):
+//   order 0: s;  order 1: s (1 + t) - g.u;
+//   order 2: s (1 + t + (t^2 + Z)/2) - g.u (1 + t)     (A1 = 1 + Z/2)
+template <class L, class R>
+struct MidState {
+  static constexpr int NS = L::NSHELL;
+  R drho, rho, u[3], theta_m1, u2, gu, cu[3], cg[3];
+  R A0[NS], A1[NS], A2[NS];
+};
+
+template <class L, class R>
+__device__ __forceinline__ void prepare_shells(MidState<L, R>& m) {
+  constexpr int D = L::D;
+  const R Th = m.theta_m1, u2 = m.u2;
+  static_for<0, L::NSHELL>([&](auto S) {
+    constexpr int s = S;
+    constexpr double X2d = L::c2 * double(L::E2(s));
+    constexpr F2 X2f = f2_of(X2d);
+    const R ThX2 = kmul<R>(X2d, X2f, Th);  // Th * |xi|^2, constant carried as hi + lo
+    R a0 = R(-0.5) * u2 + R(0.5) * (ThX2 - R(D) * Th);
+    R a1 = R(1) - R(0.5) * u2 + R(0.5) * (ThX2 - R(D + 2) * Th);
+    R a2 = R(0.5);
+    if constexpr (L::NEQ >= 4) {
+      constexpr double q2 = X2d * X2d - 2.0 * (D + 2) * X2d + double(D * (D + 2));
+      constexpr F2 q2f = f2_of(q2);
+      a0 += R(1.0 / 24.0) * (R(3) * u2 * u2 - R(6) * u2 * (ThX2 - R(D + 2) * Th) +
+                             R(3) * Th * kmul<R>(q2, q2f, Th));
+      a2 += R(0.25) * ((ThX2 - R(D + 4) * Th) - u2);
+    }
+    m.A0[s] = a0;
+    m.A1[s] = a1;
+    m.A2[s] = a2;
+  });
+}
+
+// Raw moments of the deviations: drho = sum d, j = sum e d, k2 = sum |e|^2 d
+// (so rho = 1 + drho, sum f xi = c j, sum f xi^2 = D + c^2 k2), summed per
+// opposite pair.
+template <class L, class R>
+struct RawMoments {
+  R drho, j[3], k2;
+};
+
+template <class L, class R>
+__device__ __forceinline__ RawMoments<L, R> raw_moments(const R (&d)[L::Q]) {
+  constexpr int Q = L::Q, D = L::D, NP = (Q - 1) / 2;
+  RawMoments<L, R> r;
+  R drho = d[0], j0 = R(0), j1 = R(0), j2 = R(0), k2 = R(0);
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    constexpr int ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
+    constexpr int e2 = ex * ex + ey * ey + ez * ez;
+    const R s = d[ip] + d[im];
+    const R a = d[ip] - d[im];
+    drho += s;
+    j0 = mac<ex>(a, j0);
+    j1 = mac<ey>(a, j1);
+    if constexpr (D == 3) j2 = mac<ez>(a, j2);
+    k2 = mac<e2>(s, k2);
+  });
+  r.drho = drho;
+  r.j[0] = j0; r.j[1] = j1; r.j[2] = j2;
+  r.k2 = k2;
+  return r;
+}
+
+// From the deviations of the pulled distribution.
+template <class L, class R>
+__device__ __forceinline__ void midpoint_state(const R (&d)[L::Q], const R (&g)[3], MidState<L, R>& m) {
+  constexpr int D = L::D;
+  const RawMoments<L, R> r = raw_moments<L, R>(d);
+  const R drho = r.drho;
+  const R rho = R(1) + drho;
+  const R irho = R(1) / rho;
+  const R ut0 = mul_c<L, R>(r.j[0] * irho), ut1 = mul_c<L, R>(r.j[1] * irho),
+          ut2 = mul_c<L, R>(r.j[2] * irho);
+  const R ut_sq = ut0 * ut0 + ut1 * ut1 + ut2 * ut2;
+  const R g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  m.drho = drho;
+  m.rho = rho;
+  m.u[0] = ut0 + R(0.5) * g[0];
+  m.u[1] = ut1 + R(0.5) * g[1];
+  m.u[2] = ut2 + R(0.5) * g[2];
+  m.theta_m1 = ((mul_c2<L, R>(r.k2) - R(D) * drho) * irho - ut_sq) * R(1.0 / D) + g2 * R(0.25 / D);
+  m.u2 = m.u[0] * m.u[0] + m.u[1] * m.u[1] + m.u[2] * m.u[2];
+  m.gu = g[0] * m.u[0] + g[1] * m.u[1] + g[2] * m.u[2];
+  for (int a = 0; a < 3; ++a) {
+    m.cu[a] = mul_c<L, R>(m.u[a]);
+    m.cg[a] = mul_c<L, R>(g[a]);
+  }
+  prepare_shells<L, R>(m);
+}
+
+// From given physical fields (initialisation): drho = rho - 1 and
+// theta_m1 = T - 1 are formed in double by the caller, so that the small
+// deviations keep their precision when R is float.
+template <class L, class R>
+__device__ __forceinline__ void given_state(R drho, const R (&u)[3], R theta_m1, const R (&g)[3],
+                                            MidState<L, R>& m) {
+  m.drho = drho;
+  m.rho = R(1) + drho;
+  m.theta_m1 = theta_m1;
+  for (int a = 0; a < 3; ++a) {
+    m.u[a] = u[a];
+    m.cu[a] = mul_c<L, R>(u[a]);
+    m.cg[a] = mul_c<L, R>(g[a]);
+  }
+  m.u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  m.gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+  prepare_shells<L, R>(m);
+}
+
+// Equilibrium and force polynomials for the pair (e, -e) of direction IP:
+// p(+-) = E +- O, F'(+-) = Fe +- Fo  (F' = F/(w rho)).
+template <class L, int FO, int IP, class R>
+__device__ __forceinline__ void pair_terms(const MidState<L, R>& m, R& E, R& O, R& Fe, R& Fo) {
+  constexpr int s = L::SH(IP);
+  const R t = edot<L, IP>(m.cu);
+  const R tg = edot<L, IP>(m.cg);
+  const R t2 = t * t;
+  if constexpr (L::NEQ >= 4) {
+    E = fma(t2, fma(t2, R(1.0 / 24.0), m.A2[s]), m.A0[s]);
+  } else {
+    E = fma(t2, m.A2[s], m.A0[s]);
+  }
+  O = t * fma(t2, R(1.0 / 6.0), m.A1[s]);
+  if constexpr (FO == 0) {
+    Fe = R(0);
+    Fo = tg;
+  } else if constexpr (FO == 1) {
+    Fe = fma(tg, t, -m.gu);
+    Fo = tg;
+  } else {
+    Fe = fma(tg, t, -m.gu);
+    Fo = fma(tg, fma(R(0.5), t2, m.A1[s]), -m.gu * t);
+  }
+}
+
+// Rest particle: t = s = 0.
+template <class L, int FO, class R>
+__device__ __forceinline__ void rest_terms(const MidState<L, R>& m, R& E, R& Fe) {
+  E = m.A0[0];
+  Fe = FO >= 1 ? -m.gu : R(0);
+}
+
+}  // namespace lbm

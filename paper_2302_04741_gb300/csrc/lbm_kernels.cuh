@@ -1,0 +1,459 @@
+// lbm_kernels.cuh -- the kernels of one lattice, included by one .cu per lattice.
+//
+// Storage: structure of arrays, population i of site s at f[i*N + s], sites
+// row-major [nz][ny][nx] with x fastest; two buffers (ping-pong).  The stored
+// buffer holds the post-collision distribution f*; a step pulls
+// f~_i(x) = f*_i(x - e_i), collides (Eq. lbm) and stores f*_i(x) coalesced.
+//
+// Launch shape of the per-site kernels: blockDim = (bx, 1, 1) along x,
+// grid = (ceil(nx / bx), ny, nz): every block works on one row, so the
+// near-wall branch is uniform across a block.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <int I>
+__host__ __device__ constexpr int opposite() {
+  return I == 0 ? 0 : ((I & 1) ? I + 1 : I - 1);
+}
+
+__device__ __forceinline__ int wrap3(int v, int n) {
+  v += v < 0 ? n : 0;
+  v -= v >= n ? n : 0;
+  return v;
+}
+
+template <int D>
+__device__ __forceinline__ void site_force(const StepParams& p, int x, int y, int z, int site,
+                                           double (&g)[3]) {
+  if (p.gkind == G_UNIFORM) {
+    g[0] = p.g0[0]; g[1] = p.g0[1]; g[2] = p.g0[2];
+  } else if (p.gkind == G_SINE) {
+    const int k = p.gaxis == 0 ? x : (p.gaxis == 1 ? y : z);
+    const double s = __ldg(p.gtab + k);
+    g[0] = p.g0[0] * s; g[1] = p.g0[1] * s; g[2] = p.g0[2] * s;
+  } else {
+    g[0] = __ldg(p.gtab + site);
+    g[1] = __ldg(p.gtab + (size_t)p.N + site);
+    g[2] = D == 3 ? __ldg(p.gtab + 2 * (size_t)p.N + site) : 0.0;
+  }
+  if (D == 2) g[2] = 0.0;
+}
+
+// Pull of all Q populations of site (x, y, z) with the boundary rules, decoded
+// to deviations in type RR.  The wall axis is the last axis (y in 2-D, z in 3-D).
+template <class L, int P, class RR>
+__device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fin,
+                                     const StepParams& p, int x, int y, int z, RR (&d)[L::Q]) {
+  using C = Codec<P>;
+  constexpr int D = L::D, Q = L::Q;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const size_t N = (size_t)p.N;
+  const int a = D == 2 ? y : z;          // coordinate along the wall axis
+  const int nA = D == 2 ? ny : nz;
+  int xs[7], ys[7], zs[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    xs[k] = wrap3(x - (k - 3), nx);
+    ys[k] = wrap3(y - (k - 3), ny) * nx;
+    zs[k] = D == 3 ? wrap3(z - (k - 3), nz) * nx * ny : 0;
+  }
+  const bool near = p.wall != W_NONE && (a < 3 || a >= nA - 3);
+  if (!near) {
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = I;
+      constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
+      const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
+      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + off), p));
+    });
+    return;
+  }
+  // ---- a row next to a wall: slots whose source lies beyond the wall
+  const int side = a < 3 ? 0 : 1;
+  const int colbase = D == 2 ? x : (y * nx + x);     // site of the column at wall coord 0
+  const int lineA = D == 2 ? nx : nx * ny;           // stride along the wall axis
+  RR rm1 = RR(0);                                    // rho_w - 1 of the thermal wall
+  if (p.wall == W_THERMAL) {
+    RR sum = RR(0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int row = side == 0 ? r : nA - 1 - r;
+      static_for<0, Q>([&](auto J) {
+        constexpr int j = J;
+        constexpr int eA = L::E(j, D - 1);
+        if constexpr (eA != 0) {
+          const bool leaves = side == 0 ? (eA < 0 && r + eA < 0) : (eA > 0 && r - eA < 0);
+          if (leaves)
+            sum += RR(C::template decode<L, j>(C::load(fin + j * N + colbase + row * lineA), p));
+        }
+      });
+    }
+    rm1 = (RR(p.wallA[side]) + sum) * RR(p.wall_inv_den[side]);
+  }
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
+    constexpr int eA = L::E(i, D - 1);
+    const int sA = a - eA;
+    if (sA >= 0 && sA < nA) {
+      const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
+      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + off), p));
+    } else if (p.wall == W_BOUNCE) {
+      constexpr int io = opposite<i>();
+      const int mA = side == 0 ? eA - 1 - a : 2 * nA - 1 - sA;
+      d[i] = RR(C::template decode<L, io>(C::load(fin + io * N + colbase + mA * lineA), p));
+    } else {
+      d[i] = fma(rm1, RR(p.fw[side][i]), RR(p.fwd[side][i]));
+    }
+  });
+}
+
+// ------------------------------------------------------------ the step
+template <class L, int P, int FO>
+__global__ void __launch_bounds__(256) k_step(const typename Codec<P>::T* __restrict__ fin,
+                                              typename Codec<P>::T* __restrict__ fout,
+                                              const StepParams p) {
+  using C = Codec<P>;
+  using R = typename C::R;
+  constexpr int Q = L::Q, NP = (Q - 1) / 2;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int site = (z * p.ny + y) * p.nx + x;
+  const size_t N = (size_t)p.N;
+
+  R d[Q];
+  pull<L, P, R>(fin, p, x, y, z, d);
+  double gd[3];
+  site_force<L::D>(p, x, y, z, site, gd);
+  const R g[3] = {R(gd[0]), R(gd[1]), R(gd[2])};
+  MidState<L, R> m;
+  midpoint_state<L, R>(d, g, m);
+
+  // f*_i - w_i = d_i (1 - om) + w_i [om drho + rho (om p_i + (1 - om/2) F'_i)]
+  // evaluated per pair as even +- odd: the even part (density, temperature)
+  // is shared by e and -e, so its rounding errors cancel in the odd part that
+  // carries the momentum; only the final rounding of each member remains.
+  const R om = R(p.omega);
+  const R om1 = R(1) - om;
+  const R hom1 = R(0.5) * om1;
+  const R kf = R(1) - R(0.5) * om;
+  const R base = om * m.drho;
+  {
+    R E, Fe;
+    rest_terms<L, FO, R>(m, E, Fe);
+    const R v = fma(d[0], om1, mul_w<L, 0>(fma(m.rho, fma(om, E, kf * Fe), base)));
+    fout[site] = C::template encode<L, 0>(v, p);
+  }
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    R E, O, Fe, Fo;
+    pair_terms<L, FO, ip, R>(m, E, O, Fe, Fo);
+    const R Ge = fma(om, E, kf * Fe);
+    const R Go = fma(om, O, kf * Fo);
+    const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip>(fma(m.rho, Ge, base)));
+    const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip>(m.rho * Go));
+    fout[ip * N + site] = C::template encode<L, ip>(ev + od, p);
+    fout[im * N + site] = C::template encode<L, im>(ev - od, p);
+  });
+}
+
+// ------------------------------------------------------------ init
+// f~_i = f0_i(rho, u, T) - F_i(rho, u, T)/2 as deviations
+// d_i = w_i [drho + rho (p_i - F'_i/2)], placed at the slot the next pull of
+// (x, i) reads: x - e_i (periodic), or the mirrored slot of the opposite
+// direction beyond a wall.  MODE 0 only records max |d_i / w_i| (FP16 scale).
+template <class L, int FO, class R>
+__device__ __forceinline__ void init_site(const MidState<L, R>& m, R (&d)[L::Q]) {
+  constexpr int NP = (L::Q - 1) / 2;
+  {
+    R E, Fe;
+    rest_terms<L, FO, R>(m, E, Fe);
+    d[0] = mul_w<L, 0>(fma(m.rho, E - R(0.5) * Fe, m.drho));
+  }
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    R E, O, Fe, Fo;
+    pair_terms<L, FO, ip, R>(m, E, O, Fe, Fo);
+    const R ev = mul_w<L, ip>(fma(m.rho, E - R(0.5) * Fe, m.drho));
+    const R od = mul_w<L, ip>(m.rho * (O - R(0.5) * Fo));
+    d[ip] = ev + od;
+    d[im] = ev - od;
+  });
+}
+
+template <class L, int P, int MODE>
+__global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
+                                              const double* __restrict__ u,
+                                              const double* __restrict__ T,
+                                              typename Codec<P>::T* __restrict__ fout,
+                                              unsigned int* __restrict__ maxbits, int force_order,
+                                              const StepParams p) {
+  using C = Codec<P>;
+  using R = typename C::R;
+  constexpr int Q = L::Q, D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const int site = (z * ny + y) * nx + x;
+  const size_t N = (size_t)p.N;
+  double gd[3];
+  site_force<D>(p, x, y, z, site, gd);
+  const R g[3] = {R(gd[0]), R(gd[1]), R(gd[2])};
+  const R uu[3] = {R(u[site]), R(u[N + site]), D == 3 ? R(u[2 * N + site]) : R(0)};
+  MidState<L, R> m;
+  given_state<L, R>(R(rho[site] - 1.0), uu, R(T[site] - 1.0), g, m);
+  R d[Q];
+  if (force_order == 0) init_site<L, 0, R>(m, d);
+  else if (force_order == 1) init_site<L, 1, R>(m, d);
+  else init_site<L, 2, R>(m, d);
+  if (MODE == 0) {
+    float mx = 0.f;
+    static_for<0, Q>([&](auto I) {
+      constexpr int i = I;
+      mx = fmaxf(mx, (float)fabs(double(d[i]) / L::W(i)));
+    });
+    atomicMax(maxbits, __float_as_uint(mx));
+    return;
+  }
+  const int a = D == 2 ? y : z;
+  const int nA = D == 2 ? ny : nz;
+  const int lineA = D == 2 ? nx : nx * ny;
+  const int colbase = D == 2 ? x : (y * nx + x);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
+    constexpr int eA = L::E(i, D - 1);
+    const int sA = a - eA;
+    if (p.wall != W_NONE && (sA < 0 || sA >= nA)) {
+      constexpr int io = opposite<i>();
+      const int mA = sA < 0 ? eA - 1 - a : 2 * nA - 1 - sA;
+      fout[io * N + colbase + mA * lineA] = C::template encode<L, io>(d[i], p);
+    } else {
+      const int sx = wrap3(x - ex, nx);
+      const int sy = wrap3(y - ey, ny);
+      const int sz = D == 3 ? wrap3(z - ez, nz) : 0;
+      fout[i * N + (sz * ny + sy) * nx + sx] = C::template encode<L, i>(d[i], p);
+    }
+  });
+}
+
+// ------------------------------------------------------------ moments
+// Physical rho, u, T and heat flux q in double (the FP64 diagnostic):
+// q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2) |xi_i - u|^2 (xi_i - u)
+// where f~_i - f0_i + F_i/2 = d_i - w_i [drho + rho (p_i - F'_i/2)].
+template <class L, int FO>
+__device__ __forceinline__ void heat_flux(const double (&d)[L::Q], const MidState<L, double>& m,
+                                          double omega, double (&q)[3]) {
+  constexpr int NP = (L::Q - 1) / 2;
+  const double c = L::c;
+  q[0] = q[1] = q[2] = 0.0;
+  auto add = [&](double fneq, double e0, double e1, double e2) {
+    const double c0 = c * e0 - m.u[0], c1 = c * e1 - m.u[1], c2 = c * e2 - m.u[2];
+    const double w = fneq * (c0 * c0 + c1 * c1 + c2 * c2);
+    q[0] = fma(w, c0, q[0]);
+    q[1] = fma(w, c1, q[1]);
+    q[2] = fma(w, c2, q[2]);
+  };
+  {
+    double E, Fe;
+    rest_terms<L, FO, double>(m, E, Fe);
+    add(d[0] - L::W(0) * fma(m.rho, E - 0.5 * Fe, m.drho), 0, 0, 0);
+  }
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    double E, O, Fe, Fo;
+    pair_terms<L, FO, ip, double>(m, E, O, Fe, Fo);
+    constexpr double ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
+    add(d[ip] - L::W(ip) * fma(m.rho, (E + O) - 0.5 * (Fe + Fo), m.drho), ex, ey, ez);
+    add(d[im] - L::W(im) * fma(m.rho, (E - O) - 0.5 * (Fe - Fo), m.drho), -ex, -ey, -ez);
+  });
+  const double k = 0.5 * (1.0 - 0.5 * omega);
+  q[0] *= k; q[1] *= k; q[2] *= k;
+  if (L::D == 2) q[2] = 0.0;
+}
+
+template <class L, int P>
+__global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __restrict__ fin,
+                                                 double* __restrict__ rho, double* __restrict__ u,
+                                                 double* __restrict__ T, double* __restrict__ q,
+                                                 int force_order, const StepParams p) {
+  constexpr int Q = L::Q, D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int site = (z * p.ny + y) * p.nx + x;
+  const size_t N = (size_t)p.N;
+  double d[Q];
+  pull<L, P, double>(fin, p, x, y, z, d);
+  double g[3];
+  site_force<D>(p, x, y, z, site, g);
+  MidState<L, double> m;
+  midpoint_state<L, double>(d, g, m);
+  if (rho) rho[site] = m.rho;
+  if (T) T[site] = 1.0 + m.theta_m1;
+  if (u)
+    for (int a = 0; a < D; ++a) u[a * N + site] = m.u[a];
+  if (q) {
+    double qq[3];
+    if (force_order == 0) heat_flux<L, 0>(d, m, p.omega, qq);
+    else if (force_order == 1) heat_flux<L, 1>(d, m, p.omega, qq);
+    else heat_flux<L, 2>(d, m, p.omega, qq);
+    for (int a = 0; a < D; ++a) q[a * N + site] = qq[a];
+  }
+}
+
+// ------------------------------------------------- conservation sums (FP64)
+// Compensated (Neumaier two-sum) accumulation: a value is the pair (s, c)
+// with the exact sum s + c up to the rounding of c.
+struct KSum {
+  double s, c;
+};
+__device__ __forceinline__ KSum ksum_add(KSum a, double v) {
+  const double t = a.s + v;
+  const double e = fabs(a.s) >= fabs(v) ? (a.s - t) + v : (v - t) + a.s;
+  return {t, a.c + e};
+}
+__device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
+  KSum r = ksum_add(a, b.s);
+  r.c += b.c;
+  return r;
+}
+
+// Quantities reduced: 0 mass, 1..3 momentum, 4 energy; plus a count of bad sites.
+constexpr int NCONS = 5;
+
+template <int BS>
+__device__ __forceinline__ void block_reduce_store(KSum (&v)[NCONS], unsigned bad,
+                                                   double* __restrict__ part, unsigned* badcount,
+                                                   int block) {
+  __shared__ double sh_s[BS / 32][NCONS], sh_c[BS / 32][NCONS];
+  __shared__ unsigned sh_bad[BS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NCONS; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      KSum o{__shfl_down_sync(0xffffffffu, v[k].s, off), __shfl_down_sync(0xffffffffu, v[k].c, off)};
+      v[k] = ksum_merge(v[k], o);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, off);
+  if (lane == 0) {
+    for (int k = 0; k < NCONS; ++k) {
+      sh_s[warp][k] = v[k].s;
+      sh_c[warp][k] = v[k].c;
+    }
+    sh_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned b = 0;
+    for (int k = 0; k < NCONS; ++k) {
+      KSum acc{0.0, 0.0};
+      for (int w = 0; w < BS / 32; ++w) acc = ksum_merge(acc, KSum{sh_s[w][k], sh_c[w][k]});
+      part[(size_t)block * 2 * NCONS + 2 * k] = acc.s;
+      part[(size_t)block * 2 * NCONS + 2 * k + 1] = acc.c;
+    }
+    for (int w = 0; w < BS / 32; ++w) b += sh_bad[w];
+    badcount[block] = b;
+  }
+}
+
+// One block per (row tile); every thread handles one site (x < nx) or
+// contributes zeros.  Per site only the raw moments are needed, in the
+// codec's arithmetic precision: mass rho = 1 + drho, momentum
+// rho u = c j + rho g / 2, energy rho (|u|^2 + D theta) / 2 = (K + c j.g + rho |g|^2 / 2) / 2
+// with K = D + c^2 k2 (mid-point values of R1, no division).  The sums are
+// accumulated in FP64 with compensation.  part: nblocks * 2 * NCONS doubles,
+// badcount: nblocks.
+template <class L, int P>
+__global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* __restrict__ fin,
+                                                   double* __restrict__ part,
+                                                   unsigned* __restrict__ badcount,
+                                                   const StepParams p) {
+  using R = typename Codec<P>::R;
+  constexpr int Q = L::Q, D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int block = (z * gridDim.y + y) * gridDim.x + blockIdx.x;
+  KSum v[NCONS];
+  for (int k = 0; k < NCONS; ++k) v[k] = KSum{0.0, 0.0};
+  unsigned bad = 0;
+  if (x < p.nx) {
+    const int site = (z * p.ny + y) * p.nx + x;
+    R d[Q];
+    pull<L, P, R>(fin, p, x, y, z, d);
+    double g[3];
+    site_force<D>(p, x, y, z, site, g);
+    const RawMoments<L, R> r = raw_moments<L, R>(d);
+    const double rho = 1.0 + double(r.drho);
+    double jc[3], jg = 0.0, g2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      jc[a] = L::c * double(r.j[a]);
+      jg += jc[a] * g[a];
+      g2 += g[a] * g[a];
+    }
+    const double K = double(D) + L::c2 * double(r.k2);
+    v[0] = ksum_add(v[0], rho);
+    for (int a = 0; a < D; ++a) v[1 + a] = ksum_add(v[1 + a], jc[a] + 0.5 * rho * g[a]);
+    const double e = 0.5 * (K + jg + 0.5 * rho * g2);
+    v[4] = ksum_add(v[4], e);
+    // D theta = (K - |c j|^2 / rho) / rho + g^2 / 4 in the codec's precision
+    const R rr = R(rho);
+    const R th = ((R(K) - R(jc[0] * jc[0] + jc[1] * jc[1] + jc[2] * jc[2]) / rr) / rr +
+                  R(0.25 * g2)) * R(1.0 / D);
+    const bool finite = isfinite(rho) && isfinite(e) && isfinite(th);
+    bad = (!finite || !(rho > 0.0) || !(th > R(0))) ? 1u : 0u;
+  }
+  block_reduce_store<128>(v, bad, part, badcount, block);
+}
+
+// Final pass: one block of 256 threads reduces the partials in a fixed order.
+// out: 2 * NCONS doubles (s, c pairs) followed by the bad-site count (as double).
+__global__ void __launch_bounds__(256) k_conserved_final(const double* __restrict__ part,
+                                                         const unsigned* __restrict__ badcount,
+                                                         int nblocks, double* __restrict__ out);
+
+// ------------------------------------------------------ state access
+template <class L, int P>
+__global__ void __launch_bounds__(128) k_get_pulled(const typename Codec<P>::T* __restrict__ fin,
+                                                    double* __restrict__ out, const StepParams p) {
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int site = (z * p.ny + y) * p.nx + x;
+  const size_t N = (size_t)p.N;
+  double d[Q];
+  pull<L, P, double>(fin, p, x, y, z, d);
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    out[i * N + site] = L::W(i) + d[i];
+  });
+}
+
+// DIR = 0: out = decode(f) + w ; DIR = 1: f = encode(in - w)
+template <class L, int P, int DIR>
+__global__ void __launch_bounds__(128) k_state(typename Codec<P>::T* __restrict__ f,
+                                               double* __restrict__ io, const StepParams p) {
+  using C = Codec<P>;
+  constexpr int Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= p.nx) return;
+  const int site = (blockIdx.z * p.ny + blockIdx.y) * p.nx + x;
+  const size_t N = (size_t)p.N;
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    if (DIR == 0)
+      io[i * N + site] = L::W(i) + double(C::template decode<L, i>(f[i * N + site], p));
+    else
+      f[i * N + site] = C::template encode<L, i>(typename C::R(io[i * N + site] - L::W(i)), p);
+  });
+}
+
+}  // namespace lbm

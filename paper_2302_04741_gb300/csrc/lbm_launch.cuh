@@ -1,0 +1,116 @@
+// lbm_launch.cuh -- host-side launchers of one lattice's kernels (runtime
+// precision / force-order dispatch to the template instantiations).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// Function table of one lattice, filled by lattice_ops<L>().
+struct LatticeOps {
+  int Q, D;
+  cudaError_t (*step)(int P, int FO, const void* fin, void* fout, const StepParams& p, int bx,
+                      cudaStream_t s);
+  cudaError_t (*init)(int P, int mode, const double* rho, const double* u, const double* T,
+                      void* fout, unsigned* maxbits, int FO, const StepParams& p, cudaStream_t s);
+  cudaError_t (*moments)(int P, const void* fin, double* rho, double* u, double* T, double* q,
+                         int FO, const StepParams& p, cudaStream_t s);
+  cudaError_t (*conserved)(int P, const void* fin, double* part, unsigned* bad,
+                           const StepParams& p, cudaStream_t s);
+  cudaError_t (*pulled)(int P, const void* fin, double* out, const StepParams& p, cudaStream_t s);
+  cudaError_t (*state)(int P, int dir, void* f, double* io, const StepParams& p, cudaStream_t s);
+};
+
+inline dim3 row_grid(const StepParams& p, int bx) {
+  return dim3((unsigned)((p.nx + bx - 1) / bx), (unsigned)p.ny, (unsigned)p.nz);
+}
+
+template <class L>
+struct Ops {
+  template <int P>
+  using T = typename Codec<P>::T;
+
+  static cudaError_t step(int P, int FO, const void* fin, void* fout, const StepParams& p, int bx,
+                          cudaStream_t s) {
+    const dim3 g = row_grid(p, bx), b(bx);
+#define LBM_STEP_CASE(PP, FF)                                                            \
+  case PP * 3 + FF:                                                                      \
+    k_step<L, PP, FF><<<g, b, 0, s>>>((const T<PP>*)fin, (T<PP>*)fout, p);               \
+    break;
+    switch (P * 3 + FO) {
+      LBM_STEP_CASE(0, 0) LBM_STEP_CASE(0, 1) LBM_STEP_CASE(0, 2)
+      LBM_STEP_CASE(1, 0) LBM_STEP_CASE(1, 1) LBM_STEP_CASE(1, 2)
+      LBM_STEP_CASE(2, 0) LBM_STEP_CASE(2, 1) LBM_STEP_CASE(2, 2)
+      default: return cudaErrorInvalidValue;
+    }
+#undef LBM_STEP_CASE
+    return cudaGetLastError();
+  }
+
+  static cudaError_t init(int P, int mode, const double* rho, const double* u, const double* T_,
+                          void* fout, unsigned* maxbits, int FO, const StepParams& p,
+                          cudaStream_t s) {
+    const dim3 g = row_grid(p, 128), b(128);
+    if (mode == 0) {
+      k_init<L, P_FP16S, 0><<<g, b, 0, s>>>(rho, u, T_, (T<P_FP16S>*)fout, maxbits, FO, p);
+    } else if (P == P_FP64) {
+      k_init<L, P_FP64, 1><<<g, b, 0, s>>>(rho, u, T_, (T<P_FP64>*)fout, maxbits, FO, p);
+    } else if (P == P_FP32S) {
+      k_init<L, P_FP32S, 1><<<g, b, 0, s>>>(rho, u, T_, (T<P_FP32S>*)fout, maxbits, FO, p);
+    } else {
+      k_init<L, P_FP16S, 1><<<g, b, 0, s>>>(rho, u, T_, (T<P_FP16S>*)fout, maxbits, FO, p);
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t moments(int P, const void* fin, double* rho, double* u, double* T_,
+                             double* q, int FO, const StepParams& p, cudaStream_t s) {
+    const dim3 g = row_grid(p, 128), b(128);
+    if (P == P_FP64) k_moments<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, rho, u, T_, q, FO, p);
+    else if (P == P_FP32S) k_moments<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, rho, u, T_, q, FO, p);
+    else k_moments<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, rho, u, T_, q, FO, p);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t conserved(int P, const void* fin, double* part, unsigned* bad,
+                               const StepParams& p, cudaStream_t s) {
+    const dim3 g = row_grid(p, 128), b(128);
+    if (P == P_FP64) k_conserved<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, part, bad, p);
+    else if (P == P_FP32S) k_conserved<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, part, bad, p);
+    else k_conserved<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, part, bad, p);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t pulled(int P, const void* fin, double* out, const StepParams& p,
+                            cudaStream_t s) {
+    const dim3 g = row_grid(p, 128), b(128);
+    if (P == P_FP64) k_get_pulled<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, out, p);
+    else if (P == P_FP32S) k_get_pulled<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, out, p);
+    else k_get_pulled<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, out, p);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t state(int P, int dir, void* f, double* io, const StepParams& p,
+                           cudaStream_t s) {
+    const dim3 g = row_grid(p, 128), b(128);
+#define LBM_STATE_CASE(PP)                                                                 \
+  if (P == PP) {                                                                           \
+    if (dir == 0) k_state<L, PP, 0><<<g, b, 0, s>>>((T<PP>*)f, io, p);                     \
+    else k_state<L, PP, 1><<<g, b, 0, s>>>((T<PP>*)f, io, p);                              \
+  }
+    LBM_STATE_CASE(P_FP64) LBM_STATE_CASE(P_FP32S) LBM_STATE_CASE(P_FP16S)
+#undef LBM_STATE_CASE
+    return cudaGetLastError();
+  }
+
+  static LatticeOps table() {
+    return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state};
+  }
+};
+
+const LatticeOps& ops_d2q37();
+const LatticeOps& ops_d3q39();
+
+}  // namespace lbm
