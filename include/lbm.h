@@ -179,13 +179,48 @@ int lbm_load(lbm_ctx *ctx, const char *path);
 /* Device bytes held by a context. */
 size_t lbm_device_bytes(const lbm_ctx *ctx);
 
-/* Message of the last error on ctx (or of the last failed lbm_create when
- * ctx is NULL).  Never NULL. */
+/* Message of the last error on ctx (or, when ctx is NULL, of the last failed
+ * call made without a context: lbm_create, lbm_conserved_static).  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
 /* Frees all device memory of the context and the context itself.  NULL is a
  * no-op. */
 void lbm_destroy(lbm_ctx *ctx);
+
+/* ---- Allocation-free conservation sums (no counterpart in the paper). ----
+ *
+ * For callers that must not allocate device memory: a plugin inside an
+ * application that owns every device byte through its own pool, a runtime
+ * whose memory budget is reserved up front, or a latency-sensitive loop that
+ * cannot afford cudaMalloc / cudaFree (they synchronise the whole device).
+ * Such callers cannot create an lbm_ctx, so this call takes the raw state and
+ * computes what lbm_conserved computes, with the same kernels and order.
+ *
+ *   f    device pointer to a post-collision population buffer in the
+ *        library's layout (Q*N values f[i*N + site], library direction
+ *        order) and storage format: double f_i (LBM_FP64), float f_i - w_i
+ *        (LBM_FP32_SHIFTED) or half s (f_i - w_i) / w_i (LBM_FP16_SCALED,
+ *        s = fp16_scale, ignored otherwise);
+ *   opt  precision, bc, T_lo / T_hi and stream are used (NULL: defaults);
+ *   g    NULL, LBM_G_UNIFORM, or LBM_G_FIELD with a DEVICE pointer of D*N
+ *        doubles (LBM_G_SINE is rejected: pass it as a field);
+ *   out  device pointer to 6 doubles: mass, momentum[3], energy, and the
+ *        number of sites with a non-finite moment, rho <= 0 or T <= 0.
+ *
+ * Nothing is allocated: the per-block partial sums live in a static device
+ * array of LBM_STATIC_MAX_TILES row tiles (128 sites along x each; 2.75 MB
+ * held by every GPU that loads the library until the process exits).  Grids
+ * needing more tiles, ceil(nx/128)*ny*nz > LBM_STATIC_MAX_TILES, are rejected
+ * with LBM_EINVAL.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls on a device share the one
+ * array: calls that overlap on the GPU (different streams, no ordering) race
+ * and give wrong sums.  Every partial a call reads is written by that call
+ * first, so nothing has to be cleared between calls.  Asynchronous on
+ * opt->stream; errors are described by lbm_last_error(NULL). */
+#define LBM_STATIC_MAX_TILES 32768
+int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz, const lbm_options *opt,
+                         const lbm_gfield *g, double fp16_scale, const void *f, double *out);
 
 #ifdef __cplusplus
 }

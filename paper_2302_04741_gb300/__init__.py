@@ -90,6 +90,9 @@ def lib():
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_destroy.argtypes = [_vp]
         L.lbm_destroy.restype = None
+        L.lbm_conserved_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(lbm_options), ctypes.POINTER(lbm_gfield),
+                                           ctypes.c_double, _vp, _vp]
         _lib = L
     return _lib
 
@@ -215,6 +218,19 @@ def lbm_last_error(ctx=None):
 def lbm_destroy(ctx):
     if ctx:
         lib().lbm_destroy(ctx)
+
+
+def lbm_conserved_static(lat, nx, ny, nz, opt, g, fp16_scale, f, out):
+    """Allocation-free conservation sums of a raw device population buffer
+    ``f`` into the device array ``out`` (6 doubles); see include/lbm.h.
+    ``f`` and ``out`` are device pointers (int) or CUDA tensors."""
+    gf = make_gfield(g) if isinstance(g, dict) else g
+    fp = f.data_ptr() if hasattr(f, "data_ptr") else f
+    op = out.data_ptr() if hasattr(out, "data_ptr") else out
+    _check(lib().lbm_conserved_static(lat, nx, ny, nz,
+                                      ctypes.byref(opt) if opt is not None else None,
+                                      ctypes.byref(gf) if gf is not None else None,
+                                      float(fp16_scale), fp, op))
 
 
 # ------------------------------------------------------------ convenience

@@ -596,6 +596,11 @@ void lbm_destroy(lbm_ctx* c) {
 
 }  // extern "C"
 
+namespace lbm {
+// Context-free calls report their message through lbm_last_error(NULL).
+void set_global_error(const char* msg) { g_create_error = msg; }
+}  // namespace lbm
+
 // ------------------------------------------------ final conservation pass
 namespace lbm {
 __global__ void __launch_bounds__(256) k_conserved_final(const double* __restrict__ part,

@@ -112,5 +112,6 @@ struct Ops {
 
 const LatticeOps& ops_d2q37();
 const LatticeOps& ops_d3q39();
+void set_global_error(const char* msg);
 
 }  // namespace lbm
