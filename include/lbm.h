@@ -55,7 +55,8 @@ typedef enum {
   LBM_ENOMEM = -2,    /* device or host allocation failed                    */
   LBM_ECUDA = -3,     /* a CUDA runtime call failed (message has the code)   */
   LBM_EUNSTABLE = -4, /* lbm_conserved found NaN/Inf or rho <= 0 or T <= 0   */
-  LBM_ETIMEOUT = -5,  /* a bounded device wait ran out                       */
+  LBM_ETIMEOUT = -5,  /* a bounded device wait ran out (reported by the next
+                         lbm_conserved; the results of that step are void)   */
   LBM_ESTATE = -6,    /* call out of order (e.g. lbm_step before lbm_init)   */
   LBM_EIO = -7        /* checkpoint file could not be read or written        */
 } lbm_status;
@@ -100,12 +101,22 @@ typedef struct {
   int bc[3];         /* per axis: LBM_PERIODIC | LBM_BOUNCE_BACK | LBM_THERMAL_WALL */
   double T_lo[3];    /* wall temperature at x_a = -1/2 (THERMAL_WALL)         */
   double T_hi[3];    /* wall temperature at x_a = n_a - 1/2                   */
-  void *stream;      /* cudaStream_t to issue work on; NULL = legacy default */
+  void *stream;      /* cudaStream_t to issue work on; NULL = a stream the
+                        library creates for the context                      */
   int block_x;       /* threads per block along x for the step kernel
                         (0 = library default; multiple of 32, <= 256)        */
   int graph_steps;   /* > 0: lbm_step replays a captured CUDA graph of this
                         many steps (even); 0 = plain launches                */
+  int kernel;        /* step kernel: LBM_KERNEL_AUTO (= plain), LBM_KERNEL_PLAIN
+                        (one thread per site, direct loads), or LBM_KERNEL_TMA
+                        (persistent, TMA-staged shared-memory ring; error if
+                        the grid does not qualify: FP32/FP16 storage and
+                        nx * sizeof(element) a multiple of 16 bytes)          */
+  int tma_stages;    /* shared-memory ring depth of the TMA-staged kernel
+                        (0 = library default, else 2..8)                     */
 } lbm_options;
+
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2 };
 
 /* Fills *opt with the defaults: FP64, force_order 2, no sigma, fully periodic,
  * wall temperatures 1, NULL stream, library block shape, no graph. */
@@ -162,6 +173,9 @@ int lbm_get_populations(lbm_ctx *ctx, double *out);
  * give one step of the method from an arbitrary state. */
 int lbm_get_state(lbm_ctx *ctx, double *out);
 int lbm_set_state(lbm_ctx *ctx, const double *in);
+
+/* Step kernel in use: LBM_KERNEL_PLAIN or LBM_KERNEL_TMA. */
+int lbm_step_kernel(const lbm_ctx *ctx);
 
 /* Steps taken since lbm_init / lbm_load. */
 long long lbm_step_count(const lbm_ctx *ctx);

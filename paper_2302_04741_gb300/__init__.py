@@ -27,6 +27,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 LBM_G_UNIFORM, LBM_G_SINE, LBM_G_FIELD = 0, 1, 2
 LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SCALED = 0, 1, 2
 LBM_PERIODIC, LBM_BOUNCE_BACK, LBM_THERMAL_WALL = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_TMA = 0, 1, 2
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
                 -4: "LBM_EUNSTABLE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_EIO"}
 
@@ -41,7 +42,8 @@ class lbm_options(ctypes.Structure):
                 ("include_sigma", ctypes.c_int), ("bc", ctypes.c_int * 3),
                 ("T_lo", ctypes.c_double * 3), ("T_hi", ctypes.c_double * 3),
                 ("stream", ctypes.c_void_p), ("block_x", ctypes.c_int),
-                ("graph_steps", ctypes.c_int)]
+                ("graph_steps", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("tma_stages", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -78,6 +80,7 @@ def lib():
         L.lbm_conserved.argtypes = [_vp, _dp, _dp, _dp]
         for name in ("lbm_get_populations", "lbm_get_state", "lbm_set_state"):
             getattr(L, name).argtypes = [_vp, _vp]
+        L.lbm_step_kernel.argtypes = [_vp]
         L.lbm_step_count.argtypes = [_vp]
         L.lbm_step_count.restype = ctypes.c_longlong
         L.lbm_fp16_scale.argtypes = [_vp]
@@ -191,6 +194,10 @@ def lbm_set_state(ctx, inp):
     _check(lib().lbm_set_state(ctx, _ptr(inp)), ctx)
 
 
+def lbm_step_kernel(ctx):
+    return int(lib().lbm_step_kernel(ctx))
+
+
 def lbm_step_count(ctx):
     return int(lib().lbm_step_count(ctx))
 
@@ -235,7 +242,8 @@ def lbm_conserved_static(lat, nx, ny, nz, opt, g, fp16_scale, f, out):
 
 # ------------------------------------------------------------ convenience
 def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
-            T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0):
+            T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0, kernel=LBM_KERNEL_AUTO,
+            tma_stages=0):
     o = lbm_default_options()
     o.precision = precision
     o.force_order = force_order
@@ -246,6 +254,8 @@ def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0
     o.stream = stream
     o.block_x = block_x
     o.graph_steps = graph_steps
+    o.kernel = kernel
+    o.tma_stages = tma_stages
     return o
 
 
@@ -256,7 +266,8 @@ class Sim:
     cudaStream_t (e.g. ``torch.cuda.current_stream().cuda_stream``) or None.
     """
 
-    def __init__(self, w, stream=None, block_x=0, graph_steps=0, precision=None):
+    def __init__(self, w, stream=None, block_x=0, graph_steps=0, precision=None,
+                 kernel=LBM_KERNEL_AUTO, tma_stages=0):
         self.w = w
         self.lat = w["lattice"]
         self.D, self.Q, self.c, self.e, self.wts = lbm_lattice_info(self.lat)
@@ -265,7 +276,7 @@ class Sim:
         prec = w.get("precision", LBM_FP64) if precision is None else precision
         self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
                            w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
-                           block_x, graph_steps)
+                           block_x, graph_steps, kernel, tma_stages)
         g = w.get("g")
         self._gfield = g
         self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)

@@ -1,7 +1,10 @@
 // lbm_abi.cu -- the C ABI declared in include/lbm.h: context management,
 // argument validation, device memory, launches on the context's stream.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -25,6 +28,7 @@ struct lbm_ctx {
   void* f[2] = {nullptr, nullptr};
   int cur = 0;                 // f[cur] holds the current post-collision state
   double* gtab = nullptr;      // force table / field
+  float* gtab_f = nullptr;     // its float copy (float kernels)
   double* part = nullptr;      // conservation partials (2 * NCONS per block)
   unsigned* bad = nullptr;     // bad-site counts per block
   double* dres = nullptr;      // final reduction result
@@ -40,6 +44,11 @@ struct lbm_ctx {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   size_t bytes = 0;
   int device = 0;
+  int* derr = nullptr;         // device flag set by a bounded wait that ran out
+  int* herr = nullptr;         // pinned host copy
+  bool use_tma = false;        // TMA-staged step kernel
+  CUtensorMap tmap[2];         // tensor maps of f[0], f[1]
+  int tma_grid = 0, tma_stages = 0;
   std::string err;
 };
 
@@ -145,9 +154,103 @@ void drop_graphs(lbm_ctx* c) {
     }
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Tensor maps (x, y, [z,] direction) of both population buffers for the
+// TMA-staged kernel.  Returns false when the grid does not qualify.
+template <int P>
+bool make_tensor_maps(lbm_ctx* c, std::string* why) {
+  using G = lbm::TmaGeom<P>;
+  const size_t es = G::ES;
+  if ((c->nx * es) % 16 || ((size_t)c->N * es) % 16) {
+    *why = "nx * element size is not a multiple of 16 bytes";
+    return false;
+  }
+  auto enc = tensor_map_encoder();
+  if (!enc) {
+    *why = "cuTensorMapEncodeTiled is unavailable";
+    return false;
+  }
+  const CUtensorMapDataType dt = P == lbm::P_FP16S ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  for (int k = 0; k < 2; ++k) {
+    CUresult r;
+    if (c->D == 2) {
+      cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->Q};
+      cuuint64_t strides[2] = {c->nx * es, (cuuint64_t)c->N * es};
+      cuuint32_t box[3] = {(cuuint32_t)G::RW, 1, 1};
+      cuuint32_t estr[3] = {1, 1, 1};
+      r = enc(&c->tmap[k], dt, 3, c->f[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      cuuint64_t dims[4] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->nz, (cuuint64_t)c->Q};
+      cuuint64_t strides[3] = {c->nx * es, (cuuint64_t)c->nx * c->ny * es, (cuuint64_t)c->N * es};
+      cuuint32_t box[4] = {(cuuint32_t)G::RW, 1, 1, 1};
+      cuuint32_t estr[4] = {1, 1, 1, 1};
+      r = enc(&c->tmap[k], dt, 4, c->f[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) {
+      *why = "cuTensorMapEncodeTiled rejected the layout";
+      return false;
+    }
+  }
+  return true;
+}
+
+// Chooses the step kernel; false with *why when the TMA kernel was required
+// but cannot be used.
+bool setup_step_kernel(lbm_ctx* c, std::string* why) {
+  c->use_tma = false;
+  // AUTO runs the plain kernel: on GB300 the TMA-staged variant measured ~2x
+  // slower (its 12 resident warps per SM cannot hide the collision phase);
+  // it stays available on request and to the autotuner.
+  if (c->opt.kernel != LBM_KERNEL_TMA) return true;
+  const int P = c->opt.precision;
+  bool ok = false;
+  if (P == LBM_FP32_SHIFTED) ok = make_tensor_maps<lbm::P_FP32S>(c, why);
+  else if (P == LBM_FP16_SCALED) ok = make_tensor_maps<lbm::P_FP16S>(c, why);
+  else *why = "the TMA-staged kernel serves FP32 and FP16 storage only";
+  if (ok) {
+    int bps = 0, nsm = 0;
+    c->tma_stages = c->opt.tma_stages > 0 ? c->opt.tma_stages : 3;
+    cudaError_t e = c->ops->tma_prepare(P, c->tma_stages, &bps);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess || bps < 1) {
+      cudaGetLastError();
+      *why = "the TMA-staged kernel does not fit on this device with these stages";
+      ok = false;
+    } else {
+      const long long tiles = (long long)((c->nx + lbm::TMA_W - 1) / lbm::TMA_W) * c->ny * c->nz;
+      c->tma_grid = (int)std::min<long long>(tiles, (long long)nsm * bps);
+    }
+  }
+  c->use_tma = ok;
+  return ok || c->opt.kernel == LBM_KERNEL_AUTO;
+}
+
 int launch_one_step(lbm_ctx* c) {
-  cudaError_t e = c->ops->step(c->opt.precision, c->opt.force_order, c->f[c->cur],
-                               c->f[c->cur ^ 1], c->p, c->opt.block_x, c->stream);
+  cudaError_t e =
+      c->use_tma
+          ? c->ops->step_tma(c->opt.precision, c->opt.force_order, &c->tmap[c->cur], c->f[c->cur],
+                             c->f[c->cur ^ 1], c->p, c->tma_grid, c->tma_stages, c->stream)
+          : c->ops->step(c->opt.precision, c->opt.force_order, c->f[c->cur], c->f[c->cur ^ 1], c->p,
+                         c->opt.block_x, c->stream);
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   c->cur ^= 1;
   return LBM_OK;
@@ -193,6 +296,8 @@ void lbm_default_options(lbm_options* o) {
   o->stream = nullptr;
   o->block_x = 0;
   o->graph_steps = 0;
+  o->kernel = LBM_KERNEL_AUTO;
+  o->tma_stages = 0;
 }
 
 int lbm_lattice_info(lbm_lattice lat, int* D, int* Q, double* c, int* e, double* w) {
@@ -240,6 +345,10 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     return fail(nullptr, LBM_EINVAL, "block_x must be a multiple of 32 in [32, 256] (got %d)", o.block_x);
   if (o.graph_steps < 0 || o.graph_steps % 2)
     return fail(nullptr, LBM_EINVAL, "graph_steps must be even and >= 0 (got %d)", o.graph_steps);
+  if (o.kernel < LBM_KERNEL_AUTO || o.kernel > LBM_KERNEL_TMA)
+    return fail(nullptr, LBM_EINVAL, "unknown kernel choice %d", o.kernel);
+  if (o.tma_stages != 0 && (o.tma_stages < 2 || o.tma_stages > 8))
+    return fail(nullptr, LBM_EINVAL, "tma_stages must be 0 or 2..8 (got %d)", o.tma_stages);
   lbm_gfield gf{};
   gf.kind = LBM_G_UNIFORM;
   if (g) gf = *g;
@@ -285,6 +394,8 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   p.omega = 1.0 / tau;
   p.gkind = gf.kind; p.gaxis = gf.wave_axis;
   for (int a = 0; a < 3; ++a) p.g0[a] = a < D ? gf.g0[a] : 0.0;
+  p.omega_f = (float)p.omega;
+  for (int a = 0; a < 3; ++a) p.g0_f[a] = (float)p.g0[a];
   p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
   if (wall != lbm::W_NONE) {
     if (lat == LBM_D2Q37) wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
@@ -308,6 +419,30 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     c->bytes += gb;
   }
   p.gtab = c->gtab;
+  if (c->gtab) {  // float copy of the force table for the float kernels
+    const size_t cnt = gf.kind == LBM_G_SINE ? (size_t)n[gf.wave_axis] : (size_t)D * N;
+    float* ft = nullptr;
+    double* h = (double*)std::malloc(sizeof(double) * cnt);
+    float* hf = (float*)std::malloc(sizeof(float) * cnt);
+    cudaError_t e = (h && hf) ? cudaMemcpy(h, c->gtab, sizeof(double) * cnt, cudaMemcpyDeviceToHost)
+                              : cudaErrorMemoryAllocation;
+    if (e == cudaSuccess) {
+      for (size_t k = 0; k < cnt; ++k) hf[k] = (float)h[k];
+      e = cudaMalloc(&ft, sizeof(float) * cnt);
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(ft, hf, sizeof(float) * cnt, cudaMemcpyHostToDevice);
+    std::free(h);
+    std::free(hf);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ft);
+      fail(c, LBM_ECUDA, "float force table upload failed");
+      return bail(LBM_ECUDA);
+    }
+    c->gtab_f = ft;
+    c->bytes += sizeof(float) * cnt;
+    p.gtab_f = ft;
+  }
   // reduction scratch
   c->nblk_cons = ((nx + 127) / 128) * ny * nz;
   const size_t pb = sizeof(double) * 2 * lbm::NCONS * c->nblk_cons;
@@ -320,6 +455,21 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     return bail(LBM_ENOMEM);
   }
   c->bytes += pb + sizeof(unsigned) * c->nblk_cons + sizeof(double) * (2 * lbm::NCONS + 1) + sizeof(unsigned);
+  if (cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess || cudaMemset(c->derr, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->herr, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(c, LBM_ENOMEM, "cannot allocate the error flag");
+    return bail(LBM_ENOMEM);
+  }
+  c->bytes += sizeof(int);
+  p.err = c->derr;
+  {
+    std::string why;
+    if (!setup_step_kernel(c, &why)) {
+      fail(c, LBM_EINVAL, "TMA-staged kernel unavailable: %s", why.c_str());
+      return bail(LBM_EINVAL);
+    }
+  }
   *out = c;
   return LBM_OK;
 }
@@ -423,7 +573,12 @@ int lbm_conserved(lbm_ctx* c, double* mass, double* mom, double* energy) {
   lbm::k_conserved_final<<<1, 256, 0, c->stream>>>(c->part, c->bad, c->nblk_cons, c->dres);
   LBM_CUDA(c, cudaGetLastError());
   LBM_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * (2 * lbm::NCONS + 1), cudaMemcpyDeviceToHost, c->stream));
+  LBM_CUDA(c, cudaMemcpyAsync(c->herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (*c->herr) {
+    LBM_CUDA(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
+    return fail(c, LBM_ETIMEOUT, "a bounded device wait ran out in an earlier step; its results are void");
+  }
   const double* r = c->hres;
   if (mass) *mass = r[0] + r[1];
   if (mom)
@@ -488,6 +643,11 @@ int lbm_set_state(lbm_ctx* c, const double* in) {
 }
 
 long long lbm_step_count(const lbm_ctx* c) { return c ? c->steps : 0; }
+
+int lbm_step_kernel(const lbm_ctx* c) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  return c->use_tma ? LBM_KERNEL_TMA : LBM_KERNEL_PLAIN;
+}
 
 double lbm_fp16_scale(const lbm_ctx* c) {
   return (c && c->opt.precision == LBM_FP16_SCALED) ? (double)c->p.h_scale : 0.0;
@@ -583,12 +743,15 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->f[0]);
   cudaFree(c->f[1]);
   cudaFree(c->gtab);
+  cudaFree(c->gtab_f);
   cudaFree(c->part);
   cudaFree(c->bad);
   cudaFree(c->dres);
   cudaFree(c->dmax);
   cudaFree(c->tmp);
+  cudaFree(c->derr);
   if (c->hres) cudaFreeHost(c->hres);
+  if (c->herr) cudaFreeHost(c->herr);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

@@ -41,6 +41,27 @@ struct StepParams {
   double wall_inv_den[2];
   float h_scale;      // FP16 codec scale s and 1/s
   float h_inv_scale;
+  int* err;           // set to 1 by a kernel whose bounded wait ran out
+  // float copies for the float kernels (no FP64 conversion on their path)
+  float omega_f;
+  float g0_f[3];
+  const float* gtab_f;  // float copy of gtab (same layout)
+};
+
+// The parameters a kernel of arithmetic type R reads.
+template <class R>
+struct ParamsOf;
+template <>
+struct ParamsOf<double> {
+  __device__ __forceinline__ static double omega(const StepParams& p) { return p.omega; }
+  __device__ __forceinline__ static double g0(const StepParams& p, int a) { return p.g0[a]; }
+  __device__ __forceinline__ static double gtab(const StepParams& p, size_t k) { return __ldg(p.gtab + k); }
+};
+template <>
+struct ParamsOf<float> {
+  __device__ __forceinline__ static float omega(const StepParams& p) { return p.omega_f; }
+  __device__ __forceinline__ static float g0(const StepParams& p, int a) { return p.g0_f[a]; }
+  __device__ __forceinline__ static float gtab(const StepParams& p, size_t k) { return __ldg(p.gtab_f + k); }
 };
 
 // ---------------------------------------------------------------- helpers

@@ -42,6 +42,25 @@ __device__ __forceinline__ void site_force(const StepParams& p, int x, int y, in
   if (D == 2) g[2] = 0.0;
 }
 
+// g(x) in the arithmetic type of the kernel (float kernels read float copies).
+template <int D, class R>
+__device__ __forceinline__ void site_force_r(const StepParams& p, int x, int y, int z, int site,
+                                             R (&g)[3]) {
+  using PP = ParamsOf<R>;
+  if (p.gkind == G_UNIFORM) {
+    g[0] = PP::g0(p, 0); g[1] = PP::g0(p, 1); g[2] = PP::g0(p, 2);
+  } else if (p.gkind == G_SINE) {
+    const int k = p.gaxis == 0 ? x : (p.gaxis == 1 ? y : z);
+    const R s = PP::gtab(p, k);
+    g[0] = PP::g0(p, 0) * s; g[1] = PP::g0(p, 1) * s; g[2] = PP::g0(p, 2) * s;
+  } else {
+    g[0] = PP::gtab(p, site);
+    g[1] = PP::gtab(p, (size_t)p.N + site);
+    g[2] = D == 3 ? PP::gtab(p, 2 * (size_t)p.N + site) : R(0);
+  }
+  if (D == 2) g[2] = R(0);
+}
+
 // Pull of all Q populations of site (x, y, z) with the boundary rules, decoded
 // to deviations in type RR.  The wall axis is the last axis (y in 2-D, z in 3-D).
 template <class L, int P, class RR>
@@ -110,54 +129,163 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
   });
 }
 
+// Pull for a warp whose 32 sites neither wrap around x nor touch a wall: every
+// source offset relative to the thread's own site, i*N + (row / plane shift)
+// - e_ix, is the same for the whole block (rows wrap only through the block's
+// y, z), so addresses are a per-thread base plus block-uniform offsets.
+template <class L, int P, class RR>
+__device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __restrict__ fsite,
+                                              const StepParams& p, int y, int z,
+                                              RR (&d)[L::Q]) {
+  using C = Codec<P>;
+  constexpr int D = L::D, Q = L::Q;
+  const long long N = p.N;
+  long long dy[7], dz[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    dy[k] = (long long)(wrap3(y - (k - 3), p.ny) - y) * p.nx;
+    dz[k] = D == 3 ? (long long)(wrap3(z - (k - 3), p.nz) - z) * p.nx * p.ny : 0;
+  }
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
+    const long long off = i * N + dz[ez + 3] + dy[ey + 3] - ex;
+    d[i] = RR(C::template decode<L, i>(C::load(fsite + off), p));
+  });
+}
+
 // ------------------------------------------------------------ the step
+// Collision of one site from its pulled deviations d (Eq. lbm) and store of
+// f*(x) at `site`; shared by the plain and the TMA-staged step kernels.
+//
+// f*_i - w_i = d_i (1 - om) + w_i [om drho + rho (om p_i + (1 - om/2) F'_i)],
+// with p_i = E +- O the equilibrium polynomial and F'_i = Fe +- Fo the force
+// polynomial of the pair (e, -e) (see MidState).  rho om and rho (1 - om/2)
+// are folded into per-shell coefficients:
+//   even: P0 + t^2 (P2 + t^2 rho om / 24) + s' t,   P0 = rho om A0 + om drho - rho k g.u,
+//   odd:  t (Q1 + t^2 rho om / 6) + s' (A1 + t^2 / 2),  Q1 = rho om A1 - rho k g.u
+//   (order 1: odd force part is s' alone and Q1 = rho om A1; order 0 also drops
+//   the even force part s' t - g.u),
+// with t = xi.u, s' = rho k xi.g, k = 1 - om/2 (force order 2; lower orders
+// drop terms).  Each pair is stored as even +- odd: the even part (density,
+// temperature) is shared by e and -e, so its rounding cancels in the odd part
+// that carries the momentum; only the final rounding of each member remains.
 template <class L, int P, int FO>
-__global__ void __launch_bounds__(256) k_step(const typename Codec<P>::T* __restrict__ fin,
+__device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
+                                              const typename Codec<P>::R (&g)[3], int site,
                                               typename Codec<P>::T* __restrict__ fout,
-                                              const StepParams p) {
+                                              const StepParams& p) {
   using C = Codec<P>;
   using R = typename C::R;
-  constexpr int Q = L::Q, NP = (Q - 1) / 2;
+  constexpr int NP = (L::Q - 1) / 2, NS = L::NSHELL, D = L::D;
+  const size_t N = (size_t)p.N;
+  const RawMoments<L, R> r = raw_moments<L, R>(d);
+  // mid-point state (R1): rho, u = u~ + g/2, theta
+  const R rho = R(1) + r.drho;
+  const R irho = R(1) / rho;
+  R u[3];
+  for (int a = 0; a < 3; ++a) u[a] = mul_c<L, R>(r.j[a] * irho) + R(0.5) * g[a];
+  const R ut0 = u[0] - R(0.5) * g[0], ut1 = u[1] - R(0.5) * g[1], ut2 = u[2] - R(0.5) * g[2];
+  const R g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  const R Th = ((mul_c2<L, R>(r.k2) - R(D) * r.drho) * irho - (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)) *
+                   R(1.0 / D) + g2 * R(0.25 / D);
+  const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const R gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+  const R om = ParamsOf<R>::omega(p);
+  const R om1 = R(1) - om;
+  const R hom1 = R(0.5) * om1;
+  const R kf = R(1) - R(0.5) * om;
+  const R rom = rho * om;
+  const R rkgu = FO >= 1 ? rho * kf * gu : R(0);
+  R cu[3], cs[3];
+  for (int a = 0; a < 3; ++a) {
+    cu[a] = mul_c<L, R>(u[a]);
+    cs[a] = mul_c<L, R>(rho * kf * g[a]);
+  }
+  // per-shell coefficients as polynomials in tx = Th |xi|^2 (constant hi + lo)
+  //   A0 = a00 + tx (c1 + tx / 8 [NEQ 4]),  A1 = b0 + tx / 2,  A2 = g0 + tx / 4 [NEQ 4]
+  R a00 = R(-0.5) * u2 - R(0.5 * D) * Th;
+  R c1 = R(0.5);
+  R g0c = R(0.5);
+  if constexpr (L::NEQ >= 4) {
+    a00 += R(0.125) * u2 * u2 + R(0.25 * (D + 2)) * Th * u2 + R(0.125 * D * (D + 2)) * Th * Th;
+    c1 += R(-0.25) * u2 - R(0.25 * (D + 2)) * Th;
+    g0c += R(-0.25) * u2 - R(0.25 * (D + 4)) * Th;
+  }
+  c1 *= Th;  // A0 = a00 + c1 X2 + Th^2 X2^2 / 8 = a00 + (c1 / Th) tx + tx^2 / 8
+  const R b0 = R(1) - R(0.5) * u2 - R(0.5 * (D + 2)) * Th;
+  R P0[NS], P2[NS], Q1[NS], A1[NS];
+  const R base = om * r.drho - rkgu;
+  // rho om multiplies every direction's equilibrium part at this site, so its
+  // rounding would act as a common factor (a coherent momentum / energy error
+  // per step): carry it as rom + rom_lo, with the exact FMA residual.
+  const R rom_lo = fma(rho, om, -rom);
+  static_for<0, NS>([&](auto S) {
+    constexpr int sh = S;
+    constexpr double X2d = L::c2 * double(L::E2(sh));
+    constexpr F2 X2f = f2_of(X2d);
+    const R tx = kmul<R>(X2d, X2f, Th);
+    R A0, A2;
+    if constexpr (L::NEQ >= 4) {
+      A0 = fma(R(0.125) * tx, tx, kmul<R>(X2d, X2f, c1) + a00);
+      A2 = fma(R(0.25), tx, g0c);
+    } else {
+      A0 = fma(R(0.5), tx, a00);
+      A2 = g0c;
+    }
+    A1[sh] = fma(R(0.5), tx, b0);
+    P0[sh] = fma(rom, A0, fma(rom_lo, A0, base));
+    P2[sh] = fma(rom, A2, rom_lo * A2);
+    Q1[sh] = fma(rom, A1[sh], fma(rom_lo, A1[sh], FO >= 2 ? -rkgu : R(0)));
+  });
+  const R P4 = L::NEQ >= 4 ? rom * R(1.0 / 24.0) : R(0);
+  const R Q3 = rom * R(1.0 / 6.0);
+  // rest particle: t = s' = 0
+  typename C::T* __restrict__ fo = fout + site;
+  fo[0] = C::template encode<L, 0>(fma(d[0], om1, mul_w<L, 0>(P0[0])), p);
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    constexpr int sh = L::SH(ip);
+    const R t = edot<L, ip>(cu);
+    const R t2 = t * t;
+    R ev_in = fma(t2, L::NEQ >= 4 ? fma(t2, P4, P2[sh]) : P2[sh], P0[sh]);
+    R od_in = t * fma(t2, Q3, Q1[sh]);
+    if constexpr (FO >= 1) {
+      const R sp = edot<L, ip>(cs);
+      ev_in = fma(sp, t, ev_in);
+      od_in = FO >= 2 ? fma(sp, fma(R(0.5), t2, A1[sh]), od_in) : od_in + sp;
+    } else {
+      od_in = od_in + edot<L, ip>(cs);
+    }
+    const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip>(ev_in));
+    const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip>(od_in));
+    fo[ip * N] = C::template encode<L, ip>(ev + od, p);
+    fo[im * N] = C::template encode<L, im>(ev - od, p);
+  });
+}
+
+// float kernels are capped at 85 registers (3 x 256 threads per SM) where
+// they do not spill; the FP64 kernel keeps its registers.
+template <class L, int P, int FO>
+__global__ void __launch_bounds__(256, P == P_FP64 ? 1 : 3)
+    k_step(const typename Codec<P>::T* __restrict__ fin, typename Codec<P>::T* __restrict__ fout,
+           const StepParams p) {
+  using R = typename Codec<P>::R;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   const int site = (z * p.ny + y) * p.nx + x;
-  const size_t N = (size_t)p.N;
-
-  R d[Q];
-  pull<L, P, R>(fin, p, x, y, z, d);
-  double gd[3];
-  site_force<L::D>(p, x, y, z, site, gd);
-  const R g[3] = {R(gd[0]), R(gd[1]), R(gd[2])};
-  MidState<L, R> m;
-  midpoint_state<L, R>(d, g, m);
-
-  // f*_i - w_i = d_i (1 - om) + w_i [om drho + rho (om p_i + (1 - om/2) F'_i)]
-  // evaluated per pair as even +- odd: the even part (density, temperature)
-  // is shared by e and -e, so its rounding errors cancel in the odd part that
-  // carries the momentum; only the final rounding of each member remains.
-  const R om = R(p.omega);
-  const R om1 = R(1) - om;
-  const R hom1 = R(0.5) * om1;
-  const R kf = R(1) - R(0.5) * om;
-  const R base = om * m.drho;
-  {
-    R E, Fe;
-    rest_terms<L, FO, R>(m, E, Fe);
-    const R v = fma(d[0], om1, mul_w<L, 0>(fma(m.rho, fma(om, E, kf * Fe), base)));
-    fout[site] = C::template encode<L, 0>(v, p);
-  }
-  static_for<0, NP>([&](auto K) {
-    constexpr int ip = 2 * K + 1, im = ip + 1;
-    R E, O, Fe, Fo;
-    pair_terms<L, FO, ip, R>(m, E, O, Fe, Fo);
-    const R Ge = fma(om, E, kf * Fe);
-    const R Go = fma(om, O, kf * Fo);
-    const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip>(fma(m.rho, Ge, base)));
-    const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip>(m.rho * Go));
-    fout[ip * N + site] = C::template encode<L, ip>(ev + od, p);
-    fout[im * N + site] = C::template encode<L, im>(ev - od, p);
-  });
+  const int a = L::D == 2 ? y : z;
+  const int nA = L::D == 2 ? p.ny : p.nz;
+  const bool near = p.wall != W_NONE && (a < 3 || a >= nA - 3);
+  const int wx0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  const bool interior = !near && wx0 >= 3 && wx0 + 31 <= p.nx - 4;
+  R d[L::Q];
+  if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
+  else pull<L, P, R>(fin, p, x, y, z, d);
+  R g[3];
+  site_force_r<L::D, R>(p, x, y, z, site, g);
+  collide_store<L, P, FO>(d, g, site, fout, p);
 }
 
 // ------------------------------------------------------------ init

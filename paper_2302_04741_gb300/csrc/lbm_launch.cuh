@@ -4,7 +4,7 @@
 
 #include <cuda_runtime.h>
 
-#include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
 
@@ -21,6 +21,11 @@ struct LatticeOps {
                            const StepParams& p, cudaStream_t s);
   cudaError_t (*pulled)(int P, const void* fin, double* out, const StepParams& p, cudaStream_t s);
   cudaError_t (*state)(int P, int dir, void* f, double* io, const StepParams& p, cudaStream_t s);
+  // TMA-staged step (FP32-shifted and FP16-scaled storage only)
+  size_t (*tma_smem)(int P, int stages);
+  cudaError_t (*tma_prepare)(int P, int stages, int* blocks_per_sm);
+  cudaError_t (*step_tma)(int P, int FO, const CUtensorMap* map, const void* fin, void* fout,
+                          const StepParams& p, int grid, int stages, cudaStream_t s);
 };
 
 inline dim3 row_grid(const StepParams& p, int bx) {
@@ -105,8 +110,50 @@ struct Ops {
     return cudaGetLastError();
   }
 
+  static size_t tma_smem(int P, int S) {
+    const size_t sb = P == P_FP16S ? tma_stage_bytes<L, P_FP16S>() : tma_stage_bytes<L, P_FP32S>();
+    return (size_t)S * sb + 2 * (size_t)S * sizeof(uint64_t) + 128;  // + alignment slack
+  }
+
+  // Opts every instantiation of precision P into `stages` stages of dynamic
+  // shared memory and returns the resident blocks per SM.
+  static cudaError_t tma_prepare(int P, int S, int* bps) {
+    const int smem = (int)tma_smem(P, S);
+    cudaError_t e = cudaSuccess;
+    int occ = 0;
+#define LBM_TMA_PREP(PP, FF)                                                                  \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step_tma<L, PP, FF>,                       \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+  if (e == cudaSuccess && FF == 2)                                                            \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step_tma<L, PP, FF>, TMA_THREADS, smem);
+    if (P == P_FP32S) { LBM_TMA_PREP(P_FP32S, 0) LBM_TMA_PREP(P_FP32S, 1) LBM_TMA_PREP(P_FP32S, 2) }
+    else if (P == P_FP16S) { LBM_TMA_PREP(P_FP16S, 0) LBM_TMA_PREP(P_FP16S, 1) LBM_TMA_PREP(P_FP16S, 2) }
+    else return cudaErrorInvalidValue;
+#undef LBM_TMA_PREP
+    *bps = occ;
+    return e;
+  }
+
+  static cudaError_t step_tma(int P, int FO, const CUtensorMap* map, const void* fin, void* fout,
+                              const StepParams& p, int grid, int S, cudaStream_t s) {
+    const size_t smem = tma_smem(P, S);
+#define LBM_TMA_CASE(PP, FF)                                                               \
+  case PP * 3 + FF:                                                                        \
+    k_step_tma<L, PP, FF><<<grid, TMA_THREADS, smem, s>>>(*map, (const T<PP>*)fin,         \
+                                                           (T<PP>*)fout, p, S);            \
+    break;
+    switch (P * 3 + FO) {
+      LBM_TMA_CASE(1, 0) LBM_TMA_CASE(1, 1) LBM_TMA_CASE(1, 2)
+      LBM_TMA_CASE(2, 0) LBM_TMA_CASE(2, 1) LBM_TMA_CASE(2, 2)
+      default: return cudaErrorInvalidValue;
+    }
+#undef LBM_TMA_CASE
+    return cudaGetLastError();
+  }
+
   static LatticeOps table() {
-    return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state};
+    return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state,
+                      &tma_smem, &tma_prepare, &step_tma};
   }
 };
 

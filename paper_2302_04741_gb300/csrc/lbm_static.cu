@@ -160,6 +160,8 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
       return set_error(LBM_EINVAL, "force kind must be UNIFORM or FIELD (a device array)");
     }
   }
+  p.omega_f = 1.0f;
+  for (int a = 0; a < 3; ++a) p.g0_f[a] = (float)p.g0[a];
   if (o.precision == LBM_FP16_SCALED) {
     if (!(fp16_scale > 0.0)) return set_error(LBM_EINVAL, "fp16_scale must be > 0");
     p.h_scale = (float)fp16_scale;

@@ -31,8 +31,34 @@ def oracle_sim(w):
     return s
 
 
-def smooth_state(lat, shape, seed, amp_u=0.02, amp_T=0.03, amp_rho=0.01):
-    """Seeded smooth-ish random initial fields (rho, u, T)."""
+def _modes(shape, seed, tag, n_modes=3):
+    """Sum of a few seeded Fourier modes of the periodic box, scaled to [-1, 1]."""
+    nx, ny, nz = shape
+    zz, yy, xx = np.indices((nz, ny, nx)).reshape(3, nx * ny * nz)
+    r = W.uniform(seed, tag, 4 * n_modes)
+    f = np.zeros(nx * ny * nz)
+    for m in range(n_modes):
+        kx, ky = 1 + int(r[4 * m] * 2), int(r[4 * m + 1] * 3)
+        kz = int(r[4 * m + 2] * 2) if nz > 1 else 0
+        ph = 2 * np.pi * r[4 * m + 3]
+        f += np.sin(2 * np.pi * (kx * xx / nx + ky * yy / ny + kz * zz / nz) + ph)
+    return f / n_modes
+
+
+def smooth_state(lat, shape, seed, amp_u=0.02, amp_T=0.03, amp_rho=0.01, noise=1e-4):
+    """Seeded resolved initial fields (rho, u, T): a few Fourier modes plus a
+    small white-noise component that still exercises every code path."""
+    D = W.dims(lat)
+    N = shape[0] * shape[1] * shape[2]
+    wn = lambda tag, n: 2 * noise * (W.uniform(seed, tag, n) - 0.5)
+    rho = 1.0 + amp_rho * _modes(shape, seed, 31) + amp_rho * wn(21, N)
+    u = np.stack([amp_u * _modes(shape, seed, 32 + a) for a in range(D)]) + amp_u * wn(22, D * N).reshape(D, N)
+    T = 1.0 + amp_T * _modes(shape, seed, 36) + amp_T * wn(23, N)
+    return rho, u, T
+
+
+def white_noise_state(lat, shape, seed, amp_u=0.02, amp_T=0.03, amp_rho=0.01):
+    """Grid-scale white-noise fields (unresolved; used only where stated)."""
     D = W.dims(lat)
     N = shape[0] * shape[1] * shape[2]
     rho = 1.0 + amp_rho * (W.uniform(seed, 21, N) - 0.5)
@@ -42,11 +68,12 @@ def smooth_state(lat, shape, seed, amp_u=0.02, amp_T=0.03, amp_rho=0.01):
 
 
 def workload(lat, shape, tau=0.8, g=None, seed=1, precision=0, force_order=2, bc=(0, 0, 0),
-             T_lo=(1.0, 1.0, 1.0), T_hi=(1.0, 1.0, 1.0), **amps):
+             T_lo=(1.0, 1.0, 1.0), T_hi=(1.0, 1.0, 1.0), white_noise=False, **amps):
     D = W.dims(lat)
     if g is None:
         g = {"kind": W.G_UNIFORM, "g0": (2e-5, -1e-5, 5e-6)[:D] + (0.0,) * (3 - D)}
-    rho, u, T = smooth_state(lat, shape, seed, **amps)
+    make = white_noise_state if white_noise else smooth_state
+    rho, u, T = make(lat, shape, seed, **amps)
     return dict(lattice=lat, shape=shape, tau=tau, g=g, precision=precision,
                 force_order=force_order, bc=bc, T_lo=T_lo, T_hi=T_hi, rho=rho, u=u, T=T,
                 name=f"test_{lat}_{shape}")
