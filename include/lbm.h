@@ -201,6 +201,51 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * no-op. */
 void lbm_destroy(lbm_ctx *ctx);
 
+/* ---- Batches: many grids, one persistent launch per step. ----
+ *
+ * Not in the paper (whose runs are single grids): independent simulations of
+ * differing sizes and parameters are stepped together by one persistent
+ * kernel that strides over the row tiles of all member grids, so small grids
+ * share the GPU instead of each paying a full launch.  Every site goes
+ * through the same device code as lbm_step, so a grid's state after n batch
+ * steps is bit-identical to n lbm_step calls on it alone.
+ *
+ * Members must be initialised contexts of the batch's lattice, precision
+ * (FP32-shifted or FP16-scaled) and force order, created with the batch's
+ * stream and on its device; a context belongs to at most one batch, and
+ * lbm_step on a member returns LBM_ESTATE (lbm_moments, lbm_conserved,
+ * lbm_get_* and lbm_init still work; they are ordered on the shared stream).
+ * lbm_destroy on a member removes it from its batch first. */
+typedef struct lbm_batch lbm_batch;
+
+/* capacity: maximum number of members (device table size). */
+int lbm_batch_create(lbm_lattice lat, int precision, int force_order, void *stream, int capacity,
+                     lbm_batch **out);
+int lbm_batch_add(lbm_batch *b, lbm_ctx *ctx);
+int lbm_batch_remove(lbm_batch *b, lbm_ctx *ctx);
+int lbm_batch_size(const lbm_batch *b);
+
+/* Launch configuration: threads per block along x (multiple of 32, <= 256),
+ * sites per thread (1 or 2; a tile is block_x * sites_per_thread sites of
+ * one row), and graph_steps > 0 (even) to replay a captured CUDA graph of
+ * that many launches.  Defaults: 128, 1, 0. */
+int lbm_batch_set_config(lbm_batch *b, int block_x, int sites_per_thread, int graph_steps);
+int lbm_batch_get_config(const lbm_batch *b, int *block_x, int *sites_per_thread, int *graph_steps);
+
+/* Advances every member by n steps (asynchronous on the batch's stream). */
+int lbm_batch_step(lbm_batch *b, int n);
+
+/* Autotuner: times trial_steps (even) batch steps for each block width in
+ * {64, 128, 256} and 1 or 2 sites per thread, keeps the fastest, and caches
+ * the choice per (lattice, precision, force order, member grid shapes) for
+ * the process.  The trials are real steps: every member advances by
+ * 6 * (trial_steps + 2) steps when the timing runs (0 on a cache hit).  The
+ * chosen block width and sites per thread are returned (may be NULL). */
+int lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_x, int *sites_per_thread);
+
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* ---- Allocation-free conservation sums (no counterpart in the paper). ----
  *
  * For callers that must not allocate device memory: a plugin inside an

@@ -93,6 +93,21 @@ def lib():
         L.lbm_last_error.restype = ctypes.c_char_p
         L.lbm_destroy.argtypes = [_vp]
         L.lbm_destroy.restype = None
+        L.lbm_batch_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                                       ctypes.POINTER(_vp)]
+        for name in ("lbm_batch_add", "lbm_batch_remove"):
+            getattr(L, name).argtypes = [_vp, _vp]
+        L.lbm_batch_size.argtypes = [_vp]
+        L.lbm_batch_set_config.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.lbm_batch_get_config.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]
+        L.lbm_batch_step.argtypes = [_vp, ctypes.c_int]
+        L.lbm_batch_tune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int)]
+        L.lbm_batch_last_error.argtypes = [_vp]
+        L.lbm_batch_last_error.restype = ctypes.c_char_p
+        L.lbm_batch_destroy.argtypes = [_vp]
+        L.lbm_batch_destroy.restype = None
         L.lbm_conserved_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(lbm_options), ctypes.POINTER(lbm_gfield),
                                            ctypes.c_double, _vp, _vp]
@@ -238,6 +253,59 @@ def lbm_conserved_static(lat, nx, ny, nz, opt, g, fp16_scale, f, out):
                                       ctypes.byref(opt) if opt is not None else None,
                                       ctypes.byref(gf) if gf is not None else None,
                                       float(fp16_scale), fp, op))
+
+
+def _bcheck(rc, b):
+    if rc != LBM_OK:
+        raise LbmError(rc, lib().lbm_batch_last_error(b).decode())
+
+
+def lbm_batch_create(lat, precision, force_order=2, stream=None, capacity=1024):
+    b = _vp()
+    rc = lib().lbm_batch_create(lat, precision, force_order, stream, capacity, ctypes.byref(b))
+    _bcheck(rc, None)
+    return b
+
+
+def lbm_batch_add(b, ctx):
+    _bcheck(lib().lbm_batch_add(b, ctx), b)
+
+
+def lbm_batch_remove(b, ctx):
+    _bcheck(lib().lbm_batch_remove(b, ctx), b)
+
+
+def lbm_batch_size(b):
+    return int(lib().lbm_batch_size(b))
+
+
+def lbm_batch_set_config(b, block_x=128, sites_per_thread=1, graph_steps=0):
+    _bcheck(lib().lbm_batch_set_config(b, block_x, sites_per_thread, graph_steps), b)
+
+
+def lbm_batch_get_config(b):
+    bx, spt, gs = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().lbm_batch_get_config(b, ctypes.byref(bx), ctypes.byref(spt), ctypes.byref(gs)), b)
+    return bx.value, spt.value, gs.value
+
+
+def lbm_batch_step(b, n):
+    _bcheck(lib().lbm_batch_step(b, int(n)), b)
+
+
+def lbm_batch_tune(b, trial_steps=10):
+    bx, spt = ctypes.c_int(), ctypes.c_int()
+    _bcheck(lib().lbm_batch_tune(b, int(trial_steps), ctypes.byref(bx), ctypes.byref(spt)), b)
+    return bx.value, spt.value
+
+
+def lbm_batch_last_error(b):
+    return lib().lbm_batch_last_error(b).decode()
+
+
+def lbm_batch_destroy(b):
+    if b:
+        lib().lbm_batch_destroy(b)
 
 
 # ------------------------------------------------------------ convenience

@@ -18,53 +18,26 @@
 
 using lbm::StepParams;
 
-struct lbm_ctx {
-  int lat = 0, D = 0, Q = 0, nx = 0, ny = 0, nz = 0;
-  int N = 0;
-  double tau = 0.0;
-  lbm_options opt{};
-  const lbm::LatticeOps* ops = nullptr;
-  size_t elem = 0;             // bytes per stored population value
-  void* f[2] = {nullptr, nullptr};
-  int cur = 0;                 // f[cur] holds the current post-collision state
-  double* gtab = nullptr;      // force table / field
-  float* gtab_f = nullptr;     // its float copy (float kernels)
-  double* part = nullptr;      // conservation partials (2 * NCONS per block)
-  unsigned* bad = nullptr;     // bad-site counts per block
-  double* dres = nullptr;      // final reduction result
-  unsigned* dmax = nullptr;    // FP16 init: max |d/w| bits
-  double* hres = nullptr;      // pinned host copy of the result
-  double* tmp = nullptr;       // (2 + 2D) * N doubles, lazily allocated
-  int nblk_cons = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  StepParams p{};
-  bool initialised = false;
-  long long steps = 0;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  size_t bytes = 0;
-  int device = 0;
-  int* derr = nullptr;         // device flag set by a bounded wait that ran out
-  int* herr = nullptr;         // pinned host copy
-  bool use_tma = false;        // TMA-staged step kernel
-  CUtensorMap tmap[2];         // tensor maps of f[0], f[1]
-  int tma_grid = 0, tma_stages = 0;
-  std::string err;
-};
+#include "lbm_ctx.h"
 
 namespace {
 
 std::string g_create_error = "no error";
 
-int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+int vfail(lbm_ctx* c, int code, const char* fmt, va_list ap) {
   char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
   vsnprintf(buf, sizeof buf, fmt, ap);
-  va_end(ap);
   if (c) c->err = buf;
   else g_create_error = buf;
   return code;
+}
+
+int fail(lbm_ctx* c, int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  int rc = vfail(c, code, fmt, ap);
+  va_end(ap);
+  return rc;
 }
 
 #define LBM_CUDA(ctx, call)                                                                   \
@@ -514,6 +487,7 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
   if (!dev) LBM_CUDA(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed after return
   c->initialised = true;
   c->steps = 0;
+  lbm::batch_mark_dirty(c->batch);  // buffer parity and FP16 scale may have changed
   return LBM_OK;
 }
 
@@ -521,6 +495,7 @@ int lbm_step(lbm_ctx* c, int n) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0 (got %d)", n);
   if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_step before lbm_init");
+  if (c->batch) return fail(c, LBM_ESTATE, "ctx is stepped by its batch (lbm_batch_step)");
   LBM_CUDA(c, cudaSetDevice(c->device));
   int left = n;
   const int G = c->opt.graph_steps;
@@ -639,6 +614,7 @@ int lbm_set_state(lbm_ctx* c, const double* in) {
   drop_graphs(c);
   int rc = state_io(c, const_cast<double*>(in), 1);
   if (rc == LBM_OK) c->initialised = true;
+  lbm::batch_mark_dirty(c->batch);
   return rc;
 }
 
@@ -727,6 +703,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
   c->p.h_inv_scale = hd.h_inv_scale;
   c->steps = hd.steps;
   c->initialised = true;
+  lbm::batch_mark_dirty(c->batch);
   return LBM_OK;
 }
 
@@ -737,6 +714,7 @@ const char* lbm_last_error(const lbm_ctx* c) {
 
 void lbm_destroy(lbm_ctx* c) {
   if (!c) return;
+  if (c->batch) lbm::batch_detach(c->batch, c);
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graphs(c);
@@ -762,6 +740,14 @@ void lbm_destroy(lbm_ctx* c) {
 namespace lbm {
 // Context-free calls report their message through lbm_last_error(NULL).
 void set_global_error(const char* msg) { g_create_error = msg; }
+
+int ctx_fail(lbm_ctx* c, int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  int rc = vfail(c, code, fmt, ap);
+  va_end(ap);
+  return rc;
+}
 }  // namespace lbm
 
 // ------------------------------------------------ final conservation pass

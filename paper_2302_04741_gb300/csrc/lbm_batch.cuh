@@ -1,0 +1,83 @@
+// lbm_batch.cuh -- one persistent launch that steps a ragged set of grids.
+//
+// Every member grid keeps its own buffers and parameters; a device table
+// holds, per grid, its StepParams, both buffer pointers and the parity of the
+// buffer that holds its state before launch 0 of a sequence.  Launch k of a
+// sequence reads buffer (cur + k) & 1 and writes the other one.  Tiles are
+// row segments of blockDim.x * SPT sites; prefix[g] is the first global tile
+// of grid g (prefix[ngrids] = all tiles).  Persistent CTAs stride over the
+// global tiles, so grids of any mix of sizes share one launch, and every
+// site goes through exactly the device code of k_step (bit-identical
+// results to stepping each grid alone).
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+struct __align__(16) BatchGrid {
+  StepParams p;
+  void* f[2];
+  int cur;
+  int pad[3];
+};
+static_assert(sizeof(BatchGrid) % 16 == 0, "BatchGrid is copied as int4");
+
+// header[0] = number of grids, header[1] = number of tiles
+template <class L, int P, int FO, int SPT>
+__global__ void __launch_bounds__(256, 3)
+    k_step_batch(const BatchGrid* __restrict__ grids, const int* __restrict__ prefix,
+                 const int* __restrict__ header, int k) {
+  using C = Codec<P>;
+  using T = typename C::T;
+  using R = typename C::R;
+  // the parameters of the tile's grid, staged in shared memory once per tile
+  __shared__ __align__(16) BatchGrid sg;
+  const int ngrids = __ldg(header), ntiles = __ldg(header + 1);
+  const int bx = blockDim.x, TW = bx * SPT;
+  int gcur = -1;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int lo = 0, hi = ngrids;  // prefix[lo] <= t < prefix[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(prefix + mid) <= t) lo = mid;
+      else hi = mid;
+    }
+    if (lo != gcur) {  // block-uniform
+      __syncthreads();
+      const int4* src = reinterpret_cast<const int4*>(grids + lo);
+      int4* dst = reinterpret_cast<int4*>(&sg);
+      for (int w = threadIdx.x; w < (int)(sizeof(BatchGrid) / sizeof(int4)); w += bx) dst[w] = src[w];
+      __syncthreads();
+      gcur = lo;
+    }
+    const StepParams& p = sg.p;
+    const int lt = t - __ldg(prefix + lo);
+    const int ntx = (p.nx + TW - 1) / TW;
+    const int xt = lt % ntx, row = lt / ntx;
+    const int y = row % p.ny, z = row / p.ny;
+    const int par = (sg.cur + k) & 1;
+    const T* __restrict__ fin = static_cast<const T*>(sg.f[par]);
+    T* __restrict__ fout = static_cast<T*>(sg.f[par ^ 1]);
+    const int a = L::D == 2 ? y : z;
+    const int nA = L::D == 2 ? p.ny : p.nz;
+    const bool near = p.wall != W_NONE && (a < 3 || a >= nA - 3);
+#pragma unroll 1
+    for (int s = 0; s < SPT; ++s) {
+      const int xw = xt * TW + s * bx;
+      const int x = xw + threadIdx.x;
+      if (x >= p.nx) continue;
+      const int site = (z * p.ny + y) * p.nx + x;
+      const int wx0 = xw + (threadIdx.x & ~31);
+      const bool interior = !near && wx0 >= 3 && wx0 + 31 <= p.nx - 4;
+      R d[L::Q];
+      if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
+      else pull<L, P, R>(fin, p, x, y, z, d);
+      R g[3];
+      site_force_r<L::D, R>(p, x, y, z, site, g);
+      collide_store<L, P, FO>(d, g, site, fout, p);
+    }
+  }
+}
+
+}  // namespace lbm

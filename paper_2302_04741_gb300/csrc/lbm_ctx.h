@@ -1,0 +1,57 @@
+// lbm_ctx.h -- the context object behind the opaque lbm_ctx of include/lbm.h
+// (private to the library's translation units).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.cuh"
+
+struct lbm_batch;
+
+struct lbm_ctx {
+  int lat = 0, D = 0, Q = 0, nx = 0, ny = 0, nz = 0;
+  int N = 0;
+  double tau = 0.0;
+  lbm_options opt{};
+  const lbm::LatticeOps* ops = nullptr;
+  size_t elem = 0;             // bytes per stored population value
+  void* f[2] = {nullptr, nullptr};
+  int cur = 0;                 // f[cur] holds the current post-collision state
+  double* gtab = nullptr;      // force table / field
+  float* gtab_f = nullptr;     // its float copy (float kernels)
+  double* part = nullptr;      // conservation partials (2 * NCONS per block)
+  unsigned* bad = nullptr;     // bad-site counts per block
+  double* dres = nullptr;      // final reduction result
+  unsigned* dmax = nullptr;    // FP16 init: max |d/w| bits
+  double* hres = nullptr;      // pinned host copy of the result
+  double* tmp = nullptr;       // (2 + 2D) * N doubles, lazily allocated
+  int nblk_cons = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  lbm::StepParams p{};
+  bool initialised = false;
+  long long steps = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  size_t bytes = 0;
+  int device = 0;
+  int* derr = nullptr;         // device flag set by a bounded wait that ran out
+  int* herr = nullptr;         // pinned host copy
+  bool use_tma = false;        // TMA-staged step kernel
+  CUtensorMap tmap[2];         // tensor maps of f[0], f[1]
+  int tma_grid = 0, tma_stages = 0;
+  lbm_batch* batch = nullptr;  // batch this context is a member of
+  std::string err;
+};
+
+namespace lbm {
+// Error reporting shared by the ABI translation units: stores the message on
+// the context (or the global slot when ctx is NULL) and returns code.
+int ctx_fail(lbm_ctx* c, int code, const char* fmt, ...);
+// Batch hooks used by the context entry points.
+void batch_mark_dirty(lbm_batch* b);
+int batch_detach(lbm_batch* b, lbm_ctx* c);
+}  // namespace lbm

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm_batch.cuh"
 #include "lbm_tma.cuh"
 
 namespace lbm {
@@ -26,6 +27,10 @@ struct LatticeOps {
   cudaError_t (*tma_prepare)(int P, int stages, int* blocks_per_sm);
   cudaError_t (*step_tma)(int P, int FO, const CUtensorMap* map, const void* fin, void* fout,
                           const StepParams& p, int grid, int stages, cudaStream_t s);
+  // batch step (FP32-shifted and FP16-scaled storage; SPT 1 or 2)
+  cudaError_t (*batch_occupancy)(int P, int FO, int spt, int bx, int* blocks_per_sm);
+  cudaError_t (*batch_step)(int P, int FO, int spt, const BatchGrid* grids, const int* prefix,
+                            const int* header, int k, int grid, int bx, cudaStream_t s);
 };
 
 inline dim3 row_grid(const StepParams& p, int bx) {
@@ -151,9 +156,36 @@ struct Ops {
     return cudaGetLastError();
   }
 
+  template <int PP, int FF, int SS>
+  static cudaError_t batch_occ_one(int bx, int* bps) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_step_batch<L, PP, FF, SS>, bx, 0);
+  }
+
+  static cudaError_t batch_occupancy(int P, int FO, int spt, int bx, int* bps) {
+#define LBM_BOCC(PP, FF, SS) \
+  if (P == PP && FO == FF && spt == SS) return batch_occ_one<PP, FF, SS>(bx, bps);
+    LBM_BOCC(1, 0, 1) LBM_BOCC(1, 1, 1) LBM_BOCC(1, 2, 1) LBM_BOCC(1, 0, 2) LBM_BOCC(1, 1, 2) LBM_BOCC(1, 2, 2)
+    LBM_BOCC(2, 0, 1) LBM_BOCC(2, 1, 1) LBM_BOCC(2, 2, 1) LBM_BOCC(2, 0, 2) LBM_BOCC(2, 1, 2) LBM_BOCC(2, 2, 2)
+#undef LBM_BOCC
+    return cudaErrorInvalidValue;
+  }
+
+  static cudaError_t batch_step(int P, int FO, int spt, const BatchGrid* grids, const int* prefix,
+                                const int* header, int k, int grid, int bx, cudaStream_t s) {
+#define LBM_BSTEP(PP, FF, SS)                                                               \
+  if (P == PP && FO == FF && spt == SS) {                                                    \
+    k_step_batch<L, PP, FF, SS><<<grid, bx, 0, s>>>(grids, prefix, header, k);                \
+    return cudaGetLastError();                                                              \
+  }
+    LBM_BSTEP(1, 0, 1) LBM_BSTEP(1, 1, 1) LBM_BSTEP(1, 2, 1) LBM_BSTEP(1, 0, 2) LBM_BSTEP(1, 1, 2) LBM_BSTEP(1, 2, 2)
+    LBM_BSTEP(2, 0, 1) LBM_BSTEP(2, 1, 1) LBM_BSTEP(2, 2, 1) LBM_BSTEP(2, 0, 2) LBM_BSTEP(2, 1, 2) LBM_BSTEP(2, 2, 2)
+#undef LBM_BSTEP
+    return cudaErrorInvalidValue;
+  }
+
   static LatticeOps table() {
     return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state,
-                      &tma_smem, &tma_prepare, &step_tma};
+                      &tma_smem, &tma_prepare, &step_tma, &batch_occupancy, &batch_step};
   }
 };
 

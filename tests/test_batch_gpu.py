@@ -1,0 +1,137 @@
+"""Batches: one persistent launch steps many grids; each result must be
+bit-identical to the same grid stepped alone (same device code per site)."""
+import numpy as np
+import pytest
+
+import paper_2302_04741_gb300 as lbm
+from paper_2302_04741_gb300 import workloads as W
+from helpers import workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    from paper_2302_04741_gb300 import build
+    build.build()
+    return t
+
+
+def mixed_grids(precision, lat=0):
+    if lat == 0:
+        specs = [((128, 64, 1), (0, 0, 0)), ((200, 37, 1), (0, 0, 0)), ((64, 96, 1), (0, 2, 0)),
+                 ((384, 12, 1), (0, 1, 0)), ((36, 40, 1), (0, 0, 0))]
+    else:
+        specs = [((16, 16, 16), (0, 0, 0)), ((24, 12, 10), (0, 0, 2)), ((32, 8, 9), (0, 0, 0))]
+    ws = []
+    for k, (shape, bc) in enumerate(specs):
+        ws.append(workload(lat, shape, tau=0.55 + 0.1 * k, seed=40 + k, precision=precision, bc=bc,
+                           T_lo=(1.0, 1.06, 1.06), T_hi=(1.0, 0.95, 0.95),
+                           g={"kind": W.G_UNIFORM, "g0": (1e-5 * (k + 1), -2e-5, 1e-5)}))
+    return ws
+
+
+def states(sims):
+    return [s.get_state() for s in sims]
+
+
+@pytest.mark.parametrize("lat,precision", [(0, 1), (0, 2), (1, 1)])
+@pytest.mark.parametrize("cfg", [(128, 1, 0), (64, 2, 0), (256, 1, 4), (128, 2, 6)])
+def test_batch_bitwise_equals_single(torch, lat, precision, cfg):
+    stream = torch.cuda.Stream()
+    ws = mixed_grids(precision, lat)
+    members = [lbm.Sim(w, stream=stream.cuda_stream).init() for w in ws]
+    alone = [lbm.Sim(w).init() for w in ws]
+    b = lbm.lbm_batch_create(lat, precision, 2, stream.cuda_stream, 16)
+    try:
+        for m in members:
+            lbm.lbm_batch_add(b, m.ctx)
+        lbm.lbm_batch_set_config(b, *cfg)
+        lbm.lbm_batch_step(b, 9)   # odd: parities flip, table re-uploaded
+        lbm.lbm_batch_step(b, 14)  # graph replays (when configured) + remainder
+        for a in alone:
+            a.step(23)
+        for m, a in zip(members, alone):
+            assert lbm.lbm_step_count(m.ctx) == 23
+            np.testing.assert_array_equal(m.get_state(), a.get_state())
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_batch_membership_rules(torch):
+    stream = torch.cuda.Stream()
+    ws = mixed_grids(1)
+    b = lbm.lbm_batch_create(0, 1, 2, stream.cuda_stream, 2)
+    try:
+        m = [lbm.Sim(w, stream=stream.cuda_stream).init() for w in ws[:3]]
+        lbm.lbm_batch_add(b, m[0].ctx)
+        with pytest.raises(lbm.LbmError) as ei:   # already a member
+            lbm.lbm_batch_add(b, m[0].ctx)
+        assert ei.value.status == lbm.LBM_ESTATE
+        with pytest.raises(lbm.LbmError) as ei:   # members are stepped by their batch
+            m[0].step(1)
+        assert ei.value.status == lbm.LBM_ESTATE
+        other = lbm.Sim(ws[1]).init()              # another stream
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_batch_add(b, other.ctx)
+        assert ei.value.status == lbm.LBM_EINVAL
+        f64 = lbm.Sim(dict(ws[1], precision=0), stream=stream.cuda_stream).init()
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_add(b, f64.ctx)
+        lbm.lbm_batch_add(b, m[1].ctx)
+        with pytest.raises(lbm.LbmError) as ei:   # capacity 2
+            lbm.lbm_batch_add(b, m[2].ctx)
+        assert ei.value.status == lbm.LBM_ENOMEM
+        lbm.lbm_batch_remove(b, m[0].ctx)
+        m[0].step(1)                               # free again
+        m[1].close()                               # destroying a member detaches it
+        assert lbm.lbm_batch_size(b) == 0
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_create(0, 0, 2, None, 4)  # FP64 batches are not offered
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_batch_tune_then_continue(torch):
+    stream = torch.cuda.Stream()
+    ws = mixed_grids(1)
+    members = [lbm.Sim(w, stream=stream.cuda_stream).init() for w in ws]
+    alone = [lbm.Sim(w).init() for w in ws]
+    b = lbm.lbm_batch_create(0, 1, 2, stream.cuda_stream, 8)
+    try:
+        for m in members:
+            lbm.lbm_batch_add(b, m.ctx)
+        bx, spt = lbm.lbm_batch_tune(b, 4)
+        assert bx in (64, 128, 256) and spt in (1, 2)
+        assert lbm.lbm_batch_get_config(b)[:2] == (bx, spt)
+        n_tuned = lbm.lbm_step_count(members[0].ctx)
+        assert n_tuned == 6 * (4 + 2)
+        lbm.lbm_batch_step(b, 5)
+        for a in alone:
+            a.step(n_tuned + 5)
+        for m, a in zip(members, alone):
+            np.testing.assert_array_equal(m.get_state(), a.get_state())
+        # a second tune of the same mix hits the cache: no steps taken
+        lbm.lbm_batch_tune(b, 4)
+        assert lbm.lbm_step_count(members[0].ctx) == n_tuned + 5
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_reinit_member_inside_batch(torch):
+    stream = torch.cuda.Stream()
+    ws = mixed_grids(1)[:2]
+    members = [lbm.Sim(w, stream=stream.cuda_stream).init() for w in ws]
+    b = lbm.lbm_batch_create(0, 1, 2, stream.cuda_stream, 4)
+    try:
+        for m in members:
+            lbm.lbm_batch_add(b, m.ctx)
+        lbm.lbm_batch_step(b, 3)
+        members[0].init()          # back to t = 0, buffer parity reset
+        lbm.lbm_batch_step(b, 4)
+        ref = lbm.Sim(ws[0]).init()
+        ref.step(4)
+        np.testing.assert_array_equal(members[0].get_state(), ref.get_state())
+    finally:
+        lbm.lbm_batch_destroy(b)
