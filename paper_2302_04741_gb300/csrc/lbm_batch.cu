@@ -84,7 +84,7 @@ int upload(lbm_batch* b) {
     G.f[1] = c->f[1];
     G.cur = c->cur;
     b->h_prefix[g] = (int)tiles;
-    tiles += (long long)((c->nx + TW - 1) / TW) * c->ny * c->nz;
+    tiles += ((long long)c->N + TW - 1) / TW;
   }
   if (tiles >= (1LL << 31)) return bfail(b, LBM_EINVAL, "batch has too many tiles");
   b->h_prefix[n] = (int)tiles;

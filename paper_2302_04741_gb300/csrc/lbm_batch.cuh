@@ -3,9 +3,11 @@
 // Every member grid keeps its own buffers and parameters; a device table
 // holds, per grid, its StepParams, both buffer pointers and the parity of the
 // buffer that holds its state before launch 0 of a sequence.  Launch k of a
-// sequence reads buffer (cur + k) & 1 and writes the other one.  Tiles are
-// row segments of blockDim.x * SPT sites; prefix[g] is the first global tile
-// of grid g (prefix[ngrids] = all tiles).  Persistent CTAs stride over the
+// sequence reads buffer (cur + k) & 1 and writes the other one.  A tile is a
+// run of blockDim.x * SPT consecutive sites of one grid's flattened index
+// (x fastest), so grids whose rows are shorter than a block keep every
+// thread busy; prefix[g] is the first global tile of grid g (prefix[ngrids]
+// = all tiles).  Persistent CTAs stride over the
 // global tiles, so grids of any mix of sizes share one launch, and every
 // site goes through exactly the device code of k_step (bit-identical
 // results to stepping each grid alone).
@@ -25,7 +27,7 @@ static_assert(sizeof(BatchGrid) % 16 == 0, "BatchGrid is copied as int4");
 
 // header[0] = number of grids, header[1] = number of tiles
 template <class L, int P, int FO, int SPT>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, min_blocks<L, P>())
     k_step_batch(const BatchGrid* __restrict__ grids, const int* __restrict__ prefix,
                  const int* __restrict__ header, int k) {
   using C = Codec<P>;
@@ -53,23 +55,25 @@ __global__ void __launch_bounds__(256, 3)
     }
     const StepParams& p = sg.p;
     const int lt = t - __ldg(prefix + lo);
-    const int ntx = (p.nx + TW - 1) / TW;
-    const int xt = lt % ntx, row = lt / ntx;
-    const int y = row % p.ny, z = row / p.ny;
     const int par = (sg.cur + k) & 1;
     const T* __restrict__ fin = static_cast<const T*>(sg.f[par]);
     T* __restrict__ fout = static_cast<T*>(sg.f[par ^ 1]);
-    const int a = L::D == 2 ? y : z;
     const int nA = L::D == 2 ? p.ny : p.nz;
-    const bool near = p.wall != W_NONE && (a < 3 || a >= nA - 3);
 #pragma unroll 1
     for (int s = 0; s < SPT; ++s) {
-      const int xw = xt * TW + s * bx;
-      const int x = xw + threadIdx.x;
-      if (x >= p.nx) continue;
-      const int site = (z * p.ny + y) * p.nx + x;
-      const int wx0 = xw + (threadIdx.x & ~31);
-      const bool interior = !near && wx0 >= 3 && wx0 + 31 <= p.nx - 4;
+      const int wbase = lt * TW + s * bx;          // first site of this block pass
+      const int site = wbase + threadIdx.x;
+      const int site0 = wbase + (threadIdx.x & ~31);  // lane 0 of this warp
+      if (site0 >= p.N) break;                     // warp-uniform
+      // warp-uniform fast-path test from lane 0: the warp's 32 sites lie in
+      // one row, wrap around no axis in x and touch no wall
+      const int x0 = site0 % p.nx, r0 = site0 / p.nx;
+      const int a0 = L::D == 2 ? r0 % p.ny : r0 / p.ny;
+      const bool near0 = p.wall != W_NONE && (a0 < 3 || a0 >= nA - 3);
+      const bool interior = !near0 && x0 >= 3 && x0 + 31 <= p.nx - 4;
+      if (site >= p.N) continue;
+      const int x = site % p.nx, row = site / p.nx;
+      const int y = row % p.ny, z = row / p.ny;
       R d[L::Q];
       if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
       else pull<L, P, R>(fin, p, x, y, z, d);

@@ -264,10 +264,16 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   });
 }
 
-// float kernels are capped at 85 registers (3 x 256 threads per SM) where
-// they do not spill; the FP64 kernel keeps its registers.
+// Resident 256-thread blocks per SM the register cap is sized for: float
+// D2Q37 kernels fit 85 registers (3 blocks) without spilling, float D3Q39
+// kernels need up to 128 (2 blocks); FP64 kernels keep their registers.
+template <class L, int P>
+constexpr int min_blocks() {
+  return P == P_FP64 ? 1 : (L::Q > 37 ? 2 : 3);
+}
+
 template <class L, int P, int FO>
-__global__ void __launch_bounds__(256, P == P_FP64 ? 1 : 3)
+__global__ void __launch_bounds__(256, min_blocks<L, P>())
     k_step(const typename Codec<P>::T* __restrict__ fin, typename Codec<P>::T* __restrict__ fout,
            const StepParams p) {
   using R = typename Codec<P>::R;

@@ -1,0 +1,98 @@
+"""Continuous batching: requests that arrive while others run join the same
+persistent launches; every result must equal the request run alone."""
+import numpy as np
+import pytest
+
+import paper_2302_04741_gb300 as lbm
+from paper_2302_04741_gb300 import serving as S
+from paper_2302_04741_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pytest.importorskip("torch")
+    from paper_2302_04741_gb300 import build
+    build.build()
+
+
+class TickClock:
+    """Deterministic clock: every call advances time by dt seconds."""
+
+    def __init__(self, dt=0.01):
+        self.t = 0.0
+        self.dt = dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+
+def small_trace():
+    rng_sides = [16, 24, 32, 16, 24, 20]
+    steps = [60, 150, 90, 40, 110, 75]
+    arrivals = [0.0, 0.0, 0.05, 0.3, 0.31, 0.9]
+    return [dict(id=k, arrival=a, side=s, g=2e-6 * (k + 1), steps=n, tau=0.7 + 0.05 * k, seed=4)
+            for k, (s, n, a) in enumerate(zip(rng_sides, steps, arrivals))]
+
+
+def run_alone(req, precision):
+    sim = lbm.Sim(dict(req.workload, precision=precision)).init()
+    sim.step(req.steps)
+    out = sim.moments()
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [W.FP32_SHIFTED, W.FP16_SCALED])
+def test_each_result_same_alone_and_in_the_mix(precision):
+    reqs = S.requests_from_trace(small_trace(), precision)
+    srv = S.Server(precision=precision, max_slots=4, tick_steps=25, graph_steps=4)
+    try:
+        stats = srv.run(reqs, clock=TickClock())
+    finally:
+        srv.close()
+    assert stats["requests"] == len(reqs)
+    assert stats["max_resident"] >= 3          # requests overlapped on the device
+    assert all(r.admitted > r.arrival - 1e-12 for r in reqs)
+    for r in reqs:
+        alone = run_alone(r, precision)
+        for name, a in zip(("rho", "u", "T", "q"), alone):
+            np.testing.assert_array_equal(r.result[name], a, err_msg=f"request {r.id} {name}")
+
+
+def test_slot_limit_and_hbm_admission():
+    import torch
+    reqs = S.requests_from_trace(small_trace())
+    srv = S.Server(max_slots=2, tick_steps=30, graph_steps=0)
+    try:
+        stats = srv.run(reqs, clock=TickClock())
+        assert stats["requests"] == len(reqs) and stats["max_resident"] <= 2
+    finally:
+        srv.close()
+    # equal-size requests and room for exactly one of them at a time
+    reqs = S.requests_from_trace([dict(t, side=24) for t in small_trace()])
+    need = S.request_bytes(reqs[0].workload, W.FP32_SHIFTED)
+    free, _ = torch.cuda.mem_get_info()
+    srv = S.Server(max_slots=8, tick_steps=30, graph_steps=0, hbm_reserve=free - int(1.5 * need))
+    try:
+        stats = srv.run(reqs, clock=TickClock())
+        assert stats["requests"] == len(reqs) and stats["max_resident"] == 1
+    finally:
+        srv.close()
+
+
+def test_tuned_server_config():
+    srv = S.Server(max_slots=4, tick_steps=20, graph_steps=4, tune_sides=(16, 24))
+    try:
+        bx, spt, gs = srv.config
+        assert bx in (64, 128, 256) and spt in (1, 2) and gs == 4
+        reqs = S.requests_from_trace(small_trace()[:3])
+        stats = srv.run(reqs, clock=TickClock())
+        assert stats["requests"] == 3
+    finally:
+        srv.close()
+    for r in reqs:
+        alone = run_alone(r, W.FP32_SHIFTED)
+        np.testing.assert_array_equal(r.result["u"], alone[1])
