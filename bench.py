@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--inner", type=int, default=50, help="LBM steps per benchmark step")
+    ap.add_argument("--graph-steps", type=int, default=10,
+                    help="lbm_step replays CUDA graphs of this many steps (0 = plain launches)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
@@ -52,6 +54,9 @@ def parse_args():
     ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"],
                     help="step kernel of the FP32 context")
     ap.add_argument("--tma-stages", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations (Kolmogorov, ragged batch, serving, 3-D FP16)")
+    ap.add_argument("--serve-requests", type=int, default=120)
     return ap.parse_args()
 
 
@@ -195,6 +200,128 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ other configurations
+def rel_errors(a, b):
+    """Relative L2 of (rho, u, T, q); q normalised by max(||q_b||, 1e-3 Ma sqrt(size))."""
+    qf = 1e-3 * max(float(np.abs(b[1]).max()), 1e-3) * math.sqrt(b[1].size)
+    out = {}
+    for nm, x, y in zip(("rho", "u", "T", "q"), a, b):
+        fl = qf if nm == "q" else 0.0
+        out[nm] = float(np.linalg.norm(x - y) / max(np.linalg.norm(y), fl))
+    return out
+
+
+def event_time(torch, stream, fn, reps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def extra_kolmogorov(lbm, torch, W, peak):
+    """64x64 D2Q37 FP64 Kolmogorov flow, 2000 steps (L2-resident correctness case)."""
+    stream = torch.cuda.Stream()
+    w = W.kolmogorov()
+    sim = lbm.Sim(w, stream=stream.cuda_stream).init()
+    sim.step(10)
+    t = event_time(torch, stream, lambda: sim.step(2000), 1)
+    sim.close()
+    return {"workload": "kolmogorov_d2q37_64x64_fp64", "steps": 2000,
+            "mlups": 4096 * 2000 / t / 1e6, "note": "2.4 MB working set, L2-resident"}
+
+
+def extra_ragged(lbm, torch, W, peak, single_mlups, K=5, inner=10):
+    """64 periodic D2Q37 Kolmogorov grids of ragged sizes, FP32-shifted, one
+    persistent launch per step, graph replay, autotuned block / sites per thread."""
+    stream = torch.cuda.Stream()
+    ws = W.ragged_batch()
+    sims = [lbm.Sim(w, stream=stream.cuda_stream).init() for w in ws]
+    b = lbm.lbm_batch_create(W.D2Q37, W.FP32_SHIFTED, 2, stream.cuda_stream, len(ws))
+    try:
+        for s_ in sims:
+            lbm.lbm_batch_add(b, s_.ctx)
+        bx, spt = lbm.lbm_batch_tune(b, 4)
+        lbm.lbm_batch_set_config(b, bx, spt, inner)
+        lbm.lbm_batch_step(b, 2 * inner)
+        t = event_time(torch, stream, lambda: lbm.lbm_batch_step(b, inner), K)
+    finally:
+        lbm.lbm_batch_destroy(b)
+        for s_ in sims:
+            s_.close()
+    sites = sum(int(np.prod(w["shape"])) for w in ws)
+    mlups = sites * inner * K / t / 1e6
+    return {"workload": "ragged_batch_64_d2q37_fp32", "grids": len(ws), "sites": sites,
+            "mlups": mlups, "roofline_frac": mlups * 1e6 * 296 / (peak * 1e9),
+            "tuned": {"block_x": bx, "sites_per_thread": spt, "graph_steps": inner},
+            "vs_single_grid_mlups": mlups / single_mlups}
+
+
+def extra_serving(lbm, torch, W, peak, n_req):
+    """Poisson arrivals of D3Q39 periodic boxes (sides 32..96), FP32-shifted,
+    continuous batching; overloaded at the configured 200/s and at 0.5x the
+    measured capacity."""
+    from paper_2302_04741_gb300 import serving as S
+    # single-box reference rate (96^3, plain step kernel)
+    stream = torch.cuda.Stream()
+    w = W.make_request(dict(id=0, arrival=0.0, side=96, g=5e-6, steps=0, tau=0.8, seed=4))
+    sim = lbm.Sim(w, stream=stream.cuda_stream).init()
+    sim.step(10)
+    t = event_time(torch, stream, lambda: sim.step(50), 1)
+    sim.close()
+    single = 96 ** 3 * 50 / t / 1e6
+    out = {"workload": "serving_d3q39_fp32_poisson", "single_box_96_mlups": single}
+    trace = W.serving_trace(n_requests=n_req, rate=200.0)
+    srv = S.Server(max_slots=64, tick_steps=100, graph_steps=10, tune_sides=(32, 48, 64, 96))
+    try:
+        st = srv.run(S.requests_from_trace(trace))
+    finally:
+        srv.close()
+    st["offered_rate_per_s"] = 200.0
+    st["busy_vs_single_box"] = st["busy_mlups"] / single
+    out["at_200_per_s"] = st
+    cap = S.capacity_rate(st["busy_mlups"], trace)
+    n_low = max(8, n_req // 3)
+    low = S.rescale_arrivals(W.serving_trace(n_requests=n_low, rate=200.0, seed=5), 0.5 * cap)
+    srv = S.Server(max_slots=64, tick_steps=100, graph_steps=10, tune_sides=(32, 48, 64, 96))
+    try:
+        st2 = srv.run(S.requests_from_trace(low))
+    finally:
+        srv.close()
+    st2["offered_rate_per_s"] = 0.5 * cap
+    st2["busy_vs_single_box"] = st2["busy_mlups"] / single
+    out["at_half_capacity"] = st2
+    return out
+
+
+def extra_rb3d(lbm, torch, W, peak, K=20, err_steps=100):
+    """D3Q39 Rayleigh-Benard 512x512x256, FP16-scaled, z walls 1.02 / 0.98,
+    g_z = -5e-6, tau 0.55; error against the same run in FP64 on the GPU."""
+    stream = torch.cuda.Stream()
+    w16 = W.rayleigh_benard(nx=512, ny=512, nz=256, lattice=W.D3Q39, tau=0.55, g=-5e-6,
+                            T_bottom=1.02, T_top=0.98, seed=5, precision=W.FP16_SCALED)
+    N = 512 * 512 * 256
+    a = lbm.Sim(w16, stream=stream.cuda_stream).init()
+    a.step(2)
+    t = event_time(torch, stream, lambda: a.step(1), K)
+    mlups = N * K / t / 1e6
+    a.close()
+    a = lbm.Sim(w16, stream=stream.cuda_stream).init()
+    b = lbm.Sim(dict(w16, precision=W.FP64), stream=stream.cuda_stream).init()
+    a.step(err_steps)
+    b.step(err_steps)
+    errs = rel_errors(a.moments(), b.moments())
+    a.close()
+    b.close()
+    return {"workload": "rayleigh_benard_d3q39_512x512x256_fp16", "sites": N, "mlups": mlups,
+            "roofline_frac": mlups * 1e6 * 156 / (peak * 1e9),
+            "l2_vs_fp64_gpu": dict(steps=err_steps, **errs)}
+
+
 # --------------------------------------------------------------- our arm
 def time_context(lbm, torch, sim, stream, flush, K, W_, inner):
     """Times K benchmark steps (after W_ warm-up ones).  Returns total device
@@ -244,7 +371,7 @@ def run_ours(args):
     w32 = W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP32_SHIFTED, seed=2 + rank)
     kern = {"auto": lbm.LBM_KERNEL_AUTO, "plain": lbm.LBM_KERNEL_PLAIN, "tma": lbm.LBM_KERNEL_TMA}
     sim = lbm.Sim(w32, stream=stream.cuda_stream, kernel=kern[args.kernel],
-                  tma_stages=args.tma_stages).init()
+                  tma_stages=args.tma_stages, graph_steps=args.graph_steps).init()
 
     def barrier():
         if world > 1:
@@ -280,7 +407,7 @@ def run_ours(args):
     # FP64 storage, same workload (the FP32/FP64 ratio of the target)
     if not args.no_fp64:
         w64 = W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP64, seed=2 + rank)
-        sim64 = lbm.Sim(w64, stream=stream.cuda_stream).init()
+        sim64 = lbm.Sim(w64, stream=stream.cuda_stream, graph_steps=args.graph_steps).init()
         K64 = max(2, min(K, 5))
         t64, k64, _ = time_context(lbm, torch, sim64, stream, flush, K64, 1, inner)
         v64 = N * inner * K64 / (t64 / 1e3) / 1e6
@@ -332,6 +459,13 @@ def run_ours(args):
            "step": f"lbm_init(pinned host rho,u,T) + lbm_step({inner}) + lbm_moments(pinned host)"}
     e2e_sim.close()
 
+    configs = {}
+    if not args.no_extras:
+        configs["kolmogorov"] = extra_kolmogorov(lbm, torch, W, peak)
+        configs["ragged_batch"] = extra_ragged(lbm, torch, W, peak, value / world)
+        configs["serving"] = extra_serving(lbm, torch, W, peak, args.serve_requests)
+        configs["rb3d_fp16"] = extra_rb3d(lbm, torch, W, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, steps, dt, cores = oracle_rate(W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP64),
@@ -349,6 +483,7 @@ def run_ours(args):
                        "g": [0.0, -1e-5], "walls": "thermal y (1.05 / 0.95), periodic x",
                        "force_order": 2, "inner_lbm_steps_per_step": inner,
                        "step": f"lbm_step({inner}) + lbm_conserved",
+                       "graph_steps": args.graph_steps,
                        "l2": "256 MiB flush before every timed step (outside the timed interval); "
                              "working set 2 x 77.6 MB",
                        "parallelism": f"{world} independent grids" if world > 1 else "1 grid"},
@@ -356,6 +491,8 @@ def run_ours(args):
             "clocks": clk,
         }
         line.update(extra)
+        if configs:
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -416,8 +416,13 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     c->bytes += sizeof(float) * cnt;
     p.gtab_f = ft;
   }
-  // reduction scratch
-  c->nblk_cons = ((nx + 127) / 128) * ny * nz;
+  // reduction scratch: a grid-stride pass of at most 4 blocks per SM
+  {
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    const long long tiles = (long long)((nx + 127) / 128) * ny * nz;
+    c->nblk_cons = (int)std::min<long long>(tiles, 4LL * (nsm > 0 ? nsm : 1));
+  }
   const size_t pb = sizeof(double) * 2 * lbm::NCONS * c->nblk_cons;
   if (cudaMalloc(&c->part, pb) != cudaSuccess || cudaMalloc(&c->bad, sizeof(unsigned) * c->nblk_cons) != cudaSuccess ||
       cudaMalloc(&c->dres, sizeof(double) * (2 * lbm::NCONS + 1)) != cudaSuccess ||
@@ -544,7 +549,7 @@ int lbm_conserved(lbm_ctx* c, double* mass, double* mom, double* energy) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
   if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_conserved before lbm_init");
   LBM_CUDA(c, cudaSetDevice(c->device));
-  LBM_CUDA(c, c->ops->conserved(c->opt.precision, c->f[c->cur], c->part, c->bad, c->p, c->stream));
+  LBM_CUDA(c, c->ops->conserved(c->opt.precision, c->f[c->cur], c->part, c->bad, c->p, c->nblk_cons, c->stream));
   lbm::k_conserved_final<<<1, 256, 0, c->stream>>>(c->part, c->bad, c->nblk_cons, c->dres);
   LBM_CUDA(c, cudaGetLastError());
   LBM_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * (2 * lbm::NCONS + 1), cudaMemcpyDeviceToHost, c->stream));

@@ -498,13 +498,16 @@ __device__ __forceinline__ void block_reduce_store(KSum (&v)[NCONS], unsigned ba
   }
 }
 
-// One block per (row tile); every thread handles one site (x < nx) or
-// contributes zeros.  Per site only the raw moments are needed, in the
-// codec's arithmetic precision: mass rho = 1 + drho, momentum
-// rho u = c j + rho g / 2, energy rho (|u|^2 + D theta) / 2 = (K + c j.g + rho |g|^2 / 2) / 2
-// with K = D + c^2 k2 (mid-point values of R1, no division).  The sums are
-// accumulated in FP64 with compensation.  part: nblocks * 2 * NCONS doubles,
-// badcount: nblocks.
+// Grid-stride pass: block b handles row tiles b, b + gridDim.x, ... (one
+// site per thread and tile; threads past the row end contribute zeros).  Per
+// site only the raw moments are needed, in the codec's arithmetic precision:
+// mass rho = 1 + drho, momentum rho u = c j + rho g / 2, energy
+// rho (|u|^2 + D theta) / 2 = (K + c j.g + rho |g|^2 / 2) / 2 with
+// K = D + c^2 k2 (mid-point values of R1, no division).  Each thread sums its
+// sites in double; the warp, block and final merges are compensated
+// (two-sum).  The number of blocks is fixed by the caller, so the summation
+// order, and the result, are deterministic for a grid.  part:
+// gridDim.x * 2 * NCONS doubles, badcount: gridDim.x.
 template <class L, int P>
 __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* __restrict__ fin,
                                                    double* __restrict__ part,
@@ -512,13 +515,15 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
                                                    const StepParams p) {
   using R = typename Codec<P>::R;
   constexpr int Q = L::Q, D = L::D;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y, z = blockIdx.z;
-  const int block = (z * gridDim.y + y) * gridDim.x + blockIdx.x;
-  KSum v[NCONS];
-  for (int k = 0; k < NCONS; ++k) v[k] = KSum{0.0, 0.0};
+  const int ntx = (p.nx + 127) / 128;
+  const int ntiles = ntx * p.ny * p.nz;
+  double acc[NCONS] = {0.0, 0.0, 0.0, 0.0, 0.0};
   unsigned bad = 0;
-  if (x < p.nx) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int xt = t % ntx, row = t / ntx;
+    const int y = row % p.ny, z = row / p.ny;
+    const int x = xt * 128 + threadIdx.x;
+    if (x >= p.nx) continue;
     const int site = (z * p.ny + y) * p.nx + x;
     R d[Q];
     pull<L, P, R>(fin, p, x, y, z, d);
@@ -533,18 +538,20 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
       g2 += g[a] * g[a];
     }
     const double K = double(D) + L::c2 * double(r.k2);
-    v[0] = ksum_add(v[0], rho);
-    for (int a = 0; a < D; ++a) v[1 + a] = ksum_add(v[1 + a], jc[a] + 0.5 * rho * g[a]);
     const double e = 0.5 * (K + jg + 0.5 * rho * g2);
-    v[4] = ksum_add(v[4], e);
+    acc[0] += rho;
+    for (int a = 0; a < D; ++a) acc[1 + a] += jc[a] + 0.5 * rho * g[a];
+    acc[4] += e;
     // D theta = (K - |c j|^2 / rho) / rho + g^2 / 4 in the codec's precision
     const R rr = R(rho);
     const R th = ((R(K) - R(jc[0] * jc[0] + jc[1] * jc[1] + jc[2] * jc[2]) / rr) / rr +
                   R(0.25 * g2)) * R(1.0 / D);
     const bool finite = isfinite(rho) && isfinite(e) && isfinite(th);
-    bad = (!finite || !(rho > 0.0) || !(th > R(0))) ? 1u : 0u;
+    bad += (!finite || !(rho > 0.0) || !(th > R(0))) ? 1u : 0u;
   }
-  block_reduce_store<128>(v, bad, part, badcount, block);
+  KSum v[NCONS];
+  for (int k = 0; k < NCONS; ++k) v[k] = KSum{acc[k], 0.0};
+  block_reduce_store<128>(v, bad, part, badcount, blockIdx.x);
 }
 
 // Final pass: one block of 256 threads reduces the partials in a fixed order.

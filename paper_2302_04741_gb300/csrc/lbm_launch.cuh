@@ -19,7 +19,7 @@ struct LatticeOps {
   cudaError_t (*moments)(int P, const void* fin, double* rho, double* u, double* T, double* q,
                          int FO, const StepParams& p, cudaStream_t s);
   cudaError_t (*conserved)(int P, const void* fin, double* part, unsigned* bad,
-                           const StepParams& p, cudaStream_t s);
+                           const StepParams& p, int nblocks, cudaStream_t s);
   cudaError_t (*pulled)(int P, const void* fin, double* out, const StepParams& p, cudaStream_t s);
   cudaError_t (*state)(int P, int dir, void* f, double* io, const StepParams& p, cudaStream_t s);
   // TMA-staged step (FP32-shifted and FP16-scaled storage only)
@@ -84,9 +84,10 @@ struct Ops {
     return cudaGetLastError();
   }
 
+  // nblocks: blocks of the grid-stride conservation pass (partials written)
   static cudaError_t conserved(int P, const void* fin, double* part, unsigned* bad,
-                               const StepParams& p, cudaStream_t s) {
-    const dim3 g = row_grid(p, 128), b(128);
+                               const StepParams& p, int nblocks, cudaStream_t s) {
+    const dim3 g(nblocks), b(128);
     if (P == P_FP64) k_conserved<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, part, bad, p);
     else if (P == P_FP32S) k_conserved<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, part, bad, p);
     else k_conserved<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, part, bad, p);

@@ -76,6 +76,12 @@ int scratch_for_current_device(StaticScratch** out) {
   return LBM_OK;
 }
 
+int dev_of_current() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
 // out[0] mass, out[1..3] momentum, out[4] energy, out[5] number of bad sites.
 __global__ void k_static_combine(const double* __restrict__ res, double* __restrict__ out) {
   if (threadIdx.x == 0) {
@@ -173,9 +179,13 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   int rc = scratch_for_current_device(&s);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)o.stream;
-  cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, p, st);
+  // the grid-stride pass writes one partial per block: at most one per tile
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_of_current());
+  const int nblocks = (int)(tiles < 4LL * nsm ? tiles : 4LL * nsm);
+  cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, p, nblocks, st);
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "conservation kernel launch failed", e);
-  lbm::k_conserved_final<<<1, 256, 0, st>>>(s->part, s->bad, (int)tiles, s->res);
+  lbm::k_conserved_final<<<1, 256, 0, st>>>(s->part, s->bad, nblocks, s->res);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "final reduction launch failed", e);
   k_static_combine<<<1, 32, 0, st>>>(s->res, out);
