@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % HBM roofline, FP32-shifted vs FP64 at stated L2 error; serving p50/p99"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_tma.cuh", "lattice_tables.cuh"]
+KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_tma.cuh", "lbm_async.cuh",
+                  "lattice_tables.cuh"]
 
 
 def parse_args():
@@ -51,9 +52,10 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--nx", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=512)
-    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma"],
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain", "tma", "prefetch"],
                     help="step kernel of the FP32 context")
     ap.add_argument("--tma-stages", type=int, default=0)
+    ap.add_argument("--block-x", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other configurations (Kolmogorov, ragged batch, serving, 3-D FP16)")
     ap.add_argument("--serve-requests", type=int, default=120)
@@ -369,9 +371,11 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
     w32 = W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP32_SHIFTED, seed=2 + rank)
-    kern = {"auto": lbm.LBM_KERNEL_AUTO, "plain": lbm.LBM_KERNEL_PLAIN, "tma": lbm.LBM_KERNEL_TMA}
+    kern = {"auto": lbm.LBM_KERNEL_AUTO, "plain": lbm.LBM_KERNEL_PLAIN, "tma": lbm.LBM_KERNEL_TMA,
+            "prefetch": lbm.LBM_KERNEL_PREFETCH}
     sim = lbm.Sim(w32, stream=stream.cuda_stream, kernel=kern[args.kernel],
-                  tma_stages=args.tma_stages, graph_steps=args.graph_steps).init()
+                  tma_stages=args.tma_stages, graph_steps=args.graph_steps,
+                  block_x=args.block_x).init()
 
     def barrier():
         if world > 1:
@@ -399,8 +403,8 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "kernel": ("k_step_tma" if lbm.lbm_step_kernel(sim.ctx) == lbm.LBM_KERNEL_TMA
-                           else "k_step") + "<D2Q37, FP32_SHIFTED, order 2>",
+                "kernel": {lbm.LBM_KERNEL_TMA: "k_step_tma", lbm.LBM_KERNEL_PREFETCH: "k_step_async"}.get(
+                    lbm.lbm_step_kernel(sim.ctx), "k_step") + "<D2Q37, FP32_SHIFTED, order 2>",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": t_launch * 1e6}
 
     extra = {}

@@ -116,7 +116,10 @@ typedef struct {
                         (0 = library default, else 2..8)                     */
 } lbm_options;
 
-enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2 };
+enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2,
+       LBM_KERNEL_PREFETCH = 3 /* persistent; each thread prefetches its next tile's
+                                  populations into shared memory with cp.async while
+                                  colliding the current one (FP32-shifted only) */ };
 
 /* Fills *opt with the defaults: FP64, force_order 2, no sigma, fully periodic,
  * wall temperatures 1, NULL stream, library block shape, no graph. */
@@ -174,7 +177,7 @@ int lbm_get_populations(lbm_ctx *ctx, double *out);
 int lbm_get_state(lbm_ctx *ctx, double *out);
 int lbm_set_state(lbm_ctx *ctx, const double *in);
 
-/* Step kernel in use: LBM_KERNEL_PLAIN or LBM_KERNEL_TMA. */
+/* Step kernel in use: LBM_KERNEL_PLAIN, LBM_KERNEL_TMA or LBM_KERNEL_PREFETCH. */
 int lbm_step_kernel(const lbm_ctx *ctx);
 
 /* Steps taken since lbm_init / lbm_load. */

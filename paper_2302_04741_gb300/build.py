@@ -16,6 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_gb300.so")
 SOURCES = ["lbm_d2q37.cu", "lbm_d3q39.cu", "lbm_abi.cu", "lbm_static.cu", "lbm_batch.cu"]
 HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_launch.cuh", "lbm_tma.cuh", "lbm_batch.cuh",
+           "lbm_async.cuh",
            "lbm_ctx.h", "lattice_tables.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,8 +34,11 @@ def _cuda_lib_dir():
 
 
 def flags():
+    """nvcc flags; LBM_NVCC_DEFINES (e.g. "LBM_FLOAT_D2Q37_BLOCKS=4") adds -D
+    tuning definitions for experiments."""
+    extra = [f"-D{d}" for d in os.environ.get("LBM_NVCC_DEFINES", "").split() if d]
     return ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-                   "-I", os.path.join(os.path.dirname(HERE), "include")]
+                   "-I", os.path.join(os.path.dirname(HERE), "include")] + extra
 
 
 def _stale(target, deps):

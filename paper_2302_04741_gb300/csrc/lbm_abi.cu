@@ -190,6 +190,25 @@ bool make_tensor_maps(lbm_ctx* c, std::string* why) {
 // but cannot be used.
 bool setup_step_kernel(lbm_ctx* c, std::string* why) {
   c->use_tma = false;
+  c->use_async = false;
+  if (c->opt.kernel == LBM_KERNEL_PREFETCH) {
+    if (c->opt.precision != LBM_FP32_SHIFTED) {
+      *why = "the prefetching kernel serves FP32-shifted storage only";
+      return false;
+    }
+    int bps = 0, nsm = 0;
+    cudaError_t e = c->ops->async_occupancy(c->opt.force_order, c->opt.block_x, &bps);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess || bps < 1) {
+      cudaGetLastError();
+      *why = "the prefetching kernel does not fit with this block size";
+      return false;
+    }
+    const long long tiles = (long long)((c->nx + c->opt.block_x - 1) / c->opt.block_x) * c->ny * c->nz;
+    c->async_grid = (int)std::min<long long>(tiles, (long long)nsm * bps);
+    c->use_async = true;
+    return true;
+  }
   // AUTO runs the plain kernel: on GB300 the TMA-staged variant measured ~2x
   // slower (its 12 resident warps per SM cannot hide the collision phase);
   // it stays available on request and to the autotuner.
@@ -218,12 +237,16 @@ bool setup_step_kernel(lbm_ctx* c, std::string* why) {
 }
 
 int launch_one_step(lbm_ctx* c) {
-  cudaError_t e =
-      c->use_tma
-          ? c->ops->step_tma(c->opt.precision, c->opt.force_order, &c->tmap[c->cur], c->f[c->cur],
-                             c->f[c->cur ^ 1], c->p, c->tma_grid, c->tma_stages, c->stream)
-          : c->ops->step(c->opt.precision, c->opt.force_order, c->f[c->cur], c->f[c->cur ^ 1], c->p,
-                         c->opt.block_x, c->stream);
+  cudaError_t e;
+  if (c->use_tma)
+    e = c->ops->step_tma(c->opt.precision, c->opt.force_order, &c->tmap[c->cur], c->f[c->cur],
+                         c->f[c->cur ^ 1], c->p, c->tma_grid, c->tma_stages, c->stream);
+  else if (c->use_async)
+    e = c->ops->step_async(c->opt.force_order, c->f[c->cur], c->f[c->cur ^ 1], c->p, c->async_grid,
+                           c->opt.block_x, c->stream);
+  else
+    e = c->ops->step(c->opt.precision, c->opt.force_order, c->f[c->cur], c->f[c->cur ^ 1], c->p,
+                     c->opt.block_x, c->stream);
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   c->cur ^= 1;
   return LBM_OK;
@@ -318,7 +341,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     return fail(nullptr, LBM_EINVAL, "block_x must be a multiple of 32 in [32, 256] (got %d)", o.block_x);
   if (o.graph_steps < 0 || o.graph_steps % 2)
     return fail(nullptr, LBM_EINVAL, "graph_steps must be even and >= 0 (got %d)", o.graph_steps);
-  if (o.kernel < LBM_KERNEL_AUTO || o.kernel > LBM_KERNEL_TMA)
+  if (o.kernel < LBM_KERNEL_AUTO || o.kernel > LBM_KERNEL_PREFETCH)
     return fail(nullptr, LBM_EINVAL, "unknown kernel choice %d", o.kernel);
   if (o.tma_stages != 0 && (o.tma_stages < 2 || o.tma_stages > 8))
     return fail(nullptr, LBM_EINVAL, "tma_stages must be 0 or 2..8 (got %d)", o.tma_stages);
@@ -627,7 +650,7 @@ long long lbm_step_count(const lbm_ctx* c) { return c ? c->steps : 0; }
 
 int lbm_step_kernel(const lbm_ctx* c) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
-  return c->use_tma ? LBM_KERNEL_TMA : LBM_KERNEL_PLAIN;
+  return c->use_tma ? LBM_KERNEL_TMA : (c->use_async ? LBM_KERNEL_PREFETCH : LBM_KERNEL_PLAIN);
 }
 
 double lbm_fp16_scale(const lbm_ctx* c) {

@@ -43,6 +43,8 @@ struct lbm_ctx {
   bool use_tma = false;        // TMA-staged step kernel
   CUtensorMap tmap[2];         // tensor maps of f[0], f[1]
   int tma_grid = 0, tma_stages = 0;
+  bool use_async = false;      // prefetching persistent step kernel
+  int async_grid = 0;
   lbm_batch* batch = nullptr;  // batch this context is a member of
   std::string err;
 };

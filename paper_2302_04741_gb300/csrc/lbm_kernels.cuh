@@ -267,9 +267,14 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
 // Resident 256-thread blocks per SM the register cap is sized for: float
 // D2Q37 kernels fit 85 registers (3 blocks) without spilling, float D3Q39
 // kernels need up to 128 (2 blocks); FP64 kernels keep their registers.
+// LBM_FLOAT_D2Q37_BLOCKS overrides the D2Q37 float value at build time (a
+// tuning hook: 4 caps at 64 registers and accepts a small spill).
+#ifndef LBM_FLOAT_D2Q37_BLOCKS
+#define LBM_FLOAT_D2Q37_BLOCKS 3
+#endif
 template <class L, int P>
 constexpr int min_blocks() {
-  return P == P_FP64 ? 1 : (L::Q > 37 ? 2 : 3);
+  return P == P_FP64 ? 1 : (L::Q > 37 ? 2 : LBM_FLOAT_D2Q37_BLOCKS);
 }
 
 template <class L, int P, int FO>

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "lbm_async.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_tma.cuh"
 
@@ -27,6 +28,10 @@ struct LatticeOps {
   cudaError_t (*tma_prepare)(int P, int stages, int* blocks_per_sm);
   cudaError_t (*step_tma)(int P, int FO, const CUtensorMap* map, const void* fin, void* fout,
                           const StepParams& p, int grid, int stages, cudaStream_t s);
+  // prefetching persistent step (FP32-shifted storage)
+  cudaError_t (*async_occupancy)(int FO, int bx, int* blocks_per_sm);
+  cudaError_t (*step_async)(int FO, const void* fin, void* fout, const StepParams& p, int grid,
+                            int bx, cudaStream_t s);
   // batch step (FP32-shifted and FP16-scaled storage; SPT 1 or 2)
   cudaError_t (*batch_occupancy)(int P, int FO, int spt, int bx, int* blocks_per_sm);
   cudaError_t (*batch_step)(int P, int FO, int spt, const BatchGrid* grids, const int* prefix,
@@ -184,9 +189,38 @@ struct Ops {
     return cudaErrorInvalidValue;
   }
 
+  static size_t async_smem(int bx) { return 2 * (size_t)L::Q * bx * sizeof(float); }
+
+  static cudaError_t async_occupancy(int FO, int bx, int* bps) {
+    const int smem = (int)async_smem(bx);
+    cudaError_t e = cudaSuccess;
+#define LBM_AOCC(FF)                                                                            \
+  if (FO == FF) {                                                                               \
+    e = cudaFuncSetAttribute(k_step_async<L, P_FP32S, FF>,                                      \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                \
+    if (e == cudaSuccess)                                                                       \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_step_async<L, P_FP32S, FF>, bx,  \
+                                                        smem);                                  \
+    return e;                                                                                   \
+  }
+    LBM_AOCC(0) LBM_AOCC(1) LBM_AOCC(2)
+#undef LBM_AOCC
+    return cudaErrorInvalidValue;
+  }
+
+  static cudaError_t step_async(int FO, const void* fin, void* fout, const StepParams& p, int grid,
+                                int bx, cudaStream_t s) {
+    const size_t smem = async_smem(bx);
+    if (FO == 0) k_step_async<L, P_FP32S, 0><<<grid, bx, smem, s>>>((const float*)fin, (float*)fout, p);
+    else if (FO == 1) k_step_async<L, P_FP32S, 1><<<grid, bx, smem, s>>>((const float*)fin, (float*)fout, p);
+    else k_step_async<L, P_FP32S, 2><<<grid, bx, smem, s>>>((const float*)fin, (float*)fout, p);
+    return cudaGetLastError();
+  }
+
   static LatticeOps table() {
     return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state,
-                      &tma_smem, &tma_prepare, &step_tma, &batch_occupancy, &batch_step};
+                      &tma_smem, &tma_prepare, &step_tma, &async_occupancy, &step_async,
+                      &batch_occupancy, &batch_step};
   }
 };
 

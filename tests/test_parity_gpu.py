@@ -352,3 +352,17 @@ def test_kernel_selection():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.Sim(workload(0, (66, 8, 1), precision=1), kernel=lbm.LBM_KERNEL_TMA)
     assert ei.value.status == lbm.LBM_EINVAL
+
+
+@pytest.mark.parametrize("block_x", [64, 128])
+@pytest.mark.parametrize("case", TMA_CASES, ids=[c[0] for c in TMA_CASES])
+def test_prefetch_kernel_bitwise_equals_plain(case, block_x):
+    _, lat, shape, bc = case
+    w = workload(lat, shape, tau=0.7, seed=15, precision=1, force_order=2, bc=bc,
+                 T_lo=(1.0, 1.08, 1.08), T_hi=(1.0, 0.93, 0.93))
+    a = lbm.Sim(w, kernel=lbm.LBM_KERNEL_PLAIN).init()
+    b = lbm.Sim(w, kernel=lbm.LBM_KERNEL_PREFETCH, block_x=block_x).init()
+    assert lbm.lbm_step_kernel(b.ctx) == lbm.LBM_KERNEL_PREFETCH
+    a.step(7)
+    b.step(7)
+    np.testing.assert_array_equal(a.get_state(), b.get_state())
