@@ -147,6 +147,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def aggregate_ranks(elapsed_ms, units_per_rank, world, device=None):
+    """Whole-job throughput over `world` ranks that each processed
+    `units_per_rank` lattice updates in `elapsed_ms`: the slowest rank's time
+    (max all-reduce; the only collective, on the host-side timing, never on
+    the data path) divides the units of all ranks.  Returns (MLUPS, max ms)."""
+    t_max = elapsed_ms
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    return world * units_per_rank / (t_max / 1e3) / 1e6, t_max
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -388,12 +403,7 @@ def run_ours(args):
     total_ms, kern_ms, launches = time_context(lbm, torch, sim, stream, flush, K, Wm, inner)
     barrier()
     clk = clocks.stop()
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * N * inner * K / (t_max / 1e3) / 1e6
+    value, t_max = aggregate_ranks(total_ms, N * inner * K, world, device="cuda")
 
     bytes_per_launch = 2 * Q * 4 * N
     t_launch = kern_ms / 1e3 / (K * inner)
