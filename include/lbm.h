@@ -114,6 +114,12 @@ typedef struct {
                         nx * sizeof(element) a multiple of 16 bytes)          */
   int tma_stages;    /* shared-memory ring depth of the TMA-staged kernel
                         (0 = library default, else 2..8)                     */
+  double mu;         /* > 0: constant dynamic viscosity mu; every site relaxes
+                        with tau-hat = mu / (rho theta) + 1/2 at its mid-point
+                        state (the paper's validation runs set tau = mu/(rho
+                        theta) so that mu and the conductivity stay uniform,
+                        Sec. 3.1); the tau argument of lbm_create is then
+                        unused.  0: constant tau-hat = tau (default)          */
 } lbm_options;
 
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2,

@@ -53,8 +53,8 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.orc_create.restype = ctypes.c_void_p
             lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, _ip, _dp, _dp,
-                                       _dp]
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                       _ip, _dp, _dp, _dp]
             lib.orc_destroy.argtypes = [ctypes.c_void_p]
             lib.orc_init.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
             lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
@@ -149,10 +149,12 @@ class OracleSim:
     Field layout: scalars (N,), vectors (D, N) with N = nx*ny*nz and x fastest.
     ``tau`` is the collision divisor tau-hat of Eq. lbm.  ``g`` is the (D, N)
     acceleration field.  ``bc`` per axis: PERIODIC, BOUNCE_BACK, THERMAL_WALL.
+    ``mu`` > 0 selects constant dynamic viscosity: tau-hat = mu / (rho theta)
+    + 1/2 per site (the paper's validation runs); ``tau`` is then unused.
     """
 
     def __init__(self, lat, nx, ny, nz, tau, g, force_order=2, include_sigma=False,
-                 bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0), T_hi=(1.0, 1.0, 1.0)):
+                 bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0), T_hi=(1.0, 1.0, 1.0), mu=0.0):
         self.lib = _load()
         self.D, self.Q, self.c, self.e, self.w, self.neq = lattice_info(lat)
         if self.D == 2:
@@ -161,7 +163,7 @@ class OracleSim:
         self.N = nx * ny * nz
         g = _f64(np.asarray(g).reshape(self.D, self.N))
         bca = np.asarray(list(bc) + [0] * (3 - len(bc)), dtype=np.int32)
-        self.h = self.lib.orc_create(lat, nx, ny, nz, float(tau), int(force_order),
+        self.h = self.lib.orc_create(lat, nx, ny, nz, float(tau), float(mu), int(force_order),
                                      int(bool(include_sigma)), _p(bca, _ip),
                                      _p(_f64(T_lo)), _p(_f64(T_hi)), _p(g))
         if not self.h:

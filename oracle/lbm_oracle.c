@@ -45,6 +45,10 @@
  *       the same slots with rho_w f0_i(1, 0, T_wall) where rho_w makes the
  *       column's incoming mass equal its outgoing mass.
  *   R6  tau passed in is the collision divisor tau-hat of Eq. lbm.
+ *   R7  constant dynamic viscosity (the validation runs of Sec. 3 set
+ *       tau = mu / (rho theta) so that mu and lambda stay uniform): with
+ *       mu > 0 every site uses tau-hat = mu / (rho theta) + 1/2 with the
+ *       mid-point rho and theta, in the update, sigma-bar and q.
  */
 #include <math.h>
 #include <stdio.h>
@@ -276,6 +280,7 @@ typedef struct {
   int n[3];
   long N;
   double tau;
+  double mu;              /* > 0: constant dynamic viscosity (R7) */
   int force_order, include_sigma;
   int bc[3];
   double Tw[3][2];        /* wall temperature, [axis][0 = low, 1 = high] */
@@ -318,8 +323,9 @@ void orc_destroy(void *h) {
   free(S);
 }
 
-void *orc_create(int lat, int nx, int ny, int nz, double tau, int force_order, int include_sigma,
-                 const int *bc, const double *T_lo, const double *T_hi, const double *g) {
+void *orc_create(int lat, int nx, int ny, int nz, double tau, double mu, int force_order,
+                 int include_sigma, const int *bc, const double *T_lo, const double *T_hi,
+                 const double *g) {
   orc_sim *S = (orc_sim *)calloc(1, sizeof(orc_sim));
   if (!S) return NULL;
   if (orc_lattice_build(lat, &S->L)) { free(S); return NULL; }
@@ -332,6 +338,7 @@ void *orc_create(int lat, int nx, int ny, int nz, double tau, int force_order, i
   }
   S->N = (long)nx * ny * nz;
   S->tau = tau;
+  S->mu = mu > 0.0 ? mu : 0.0;
   S->force_order = force_order;
   S->include_sigma = include_sigma;
   S->wall_axis = -1;
@@ -479,16 +486,22 @@ static void sigma_bar(const orc_lattice *L, double tau, const double *ft, const 
   for (int k = 0; k < D * D; ++k) sig[k] *= -(1.0 - 0.5 / tau);
 }
 
+/* The collision divisor tau-hat at a site (R6 / R7). */
+static double site_tau(const orc_sim *S, const orc_state *m) {
+  return S->mu > 0.0 ? S->mu / (m->rho * m->theta) + 0.5 : S->tau;
+}
+
 /* One site of Eq. lbm given the pulled f~ (Q values) and g at the site. */
 static void collide(const orc_sim *S, const double *ft, const double *g, double *out,
                     orc_state *ms, double *feq_out, double *F_out, double *sig_out) {
   const orc_lattice *L = &S->L;
   double feq[ORC_QMAX], F[ORC_QMAX], sig[9];
   orc_state m = midpoint(L, ft, g);
+  const double tau = site_tau(S, &m);
   equilibrium(L, L->neq, m.rho, m.u, m.theta, feq);
   const double *sp = NULL;
   if (S->include_sigma) {
-    sigma_bar(L, S->tau, ft, feq, m.u, sig);
+    sigma_bar(L, tau, ft, feq, m.u, sig);
     sp = sig;
   } else {
     for (int k = 0; k < 9; ++k) sig[k] = 0.0;
@@ -496,7 +509,7 @@ static void collide(const orc_sim *S, const double *ft, const double *g, double 
   force(L, S->force_order, m.rho, m.u, m.theta, g, sp, F);
   if (out)
     for (int i = 0; i < L->Q; ++i)
-      out[i] = ft[i] - (ft[i] - feq[i]) / S->tau + (1.0 - 0.5 / S->tau) * F[i];
+      out[i] = ft[i] - (ft[i] - feq[i]) / tau + (1.0 - 0.5 / tau) * F[i];
   if (ms) *ms = m;
   if (feq_out) memcpy(feq_out, feq, sizeof(double) * L->Q);
   if (F_out) memcpy(F_out, F, sizeof(double) * L->Q);
@@ -591,10 +604,10 @@ int orc_moments(void *h, double *rho, double *u, double *T, double *q, double *s
         double fneq = ft[i] - feq[i] + 0.5 * F[i];
         for (int a = 0; a < D; ++a) qq[a] += fneq * c2 * c[a];
       }
-      for (int a = 0; a < D; ++a) q[a * S->N + s] = 0.5 * (1.0 - 0.5 / S->tau) * qq[a];
+      for (int a = 0; a < D; ++a) q[a * S->N + s] = 0.5 * (1.0 - 0.5 / site_tau(S, &m)) * qq[a];
     }
     if (sigma) {
-      if (!S->include_sigma) sigma_bar(L, S->tau, ft, feq, m.u, sig);
+      if (!S->include_sigma) sigma_bar(L, site_tau(S, &m), ft, feq, m.u, sig);
       for (int k = 0; k < D * D; ++k) sigma[(long)k * S->N + s] = sig[k];
     }
   }

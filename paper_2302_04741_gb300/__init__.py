@@ -43,7 +43,7 @@ class lbm_options(ctypes.Structure):
                 ("T_lo", ctypes.c_double * 3), ("T_hi", ctypes.c_double * 3),
                 ("stream", ctypes.c_void_p), ("block_x", ctypes.c_int),
                 ("graph_steps", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("tma_stages", ctypes.c_int)]
+                ("tma_stages", ctypes.c_int), ("mu", ctypes.c_double)]
 
 
 class LbmError(RuntimeError):
@@ -311,7 +311,7 @@ def lbm_batch_destroy(b):
 # ------------------------------------------------------------ convenience
 def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
             T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0, kernel=LBM_KERNEL_AUTO,
-            tma_stages=0):
+            tma_stages=0, mu=0.0):
     o = lbm_default_options()
     o.precision = precision
     o.force_order = force_order
@@ -324,6 +324,7 @@ def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0
     o.graph_steps = graph_steps
     o.kernel = kernel
     o.tma_stages = tma_stages
+    o.mu = mu
     return o
 
 
@@ -344,7 +345,7 @@ class Sim:
         prec = w.get("precision", LBM_FP64) if precision is None else precision
         self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
                            w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
-                           block_x, graph_steps, kernel, tma_stages)
+                           block_x, graph_steps, kernel, tma_stages, w.get("mu", 0.0))
         g = w.get("g")
         self._gfield = g
         self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)

@@ -294,6 +294,7 @@ void lbm_default_options(lbm_options* o) {
   o->graph_steps = 0;
   o->kernel = LBM_KERNEL_AUTO;
   o->tma_stages = 0;
+  o->mu = 0.0;
 }
 
 int lbm_lattice_info(lbm_lattice lat, int* D, int* Q, double* c, int* e, double* w) {
@@ -343,6 +344,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     return fail(nullptr, LBM_EINVAL, "graph_steps must be even and >= 0 (got %d)", o.graph_steps);
   if (o.kernel < LBM_KERNEL_AUTO || o.kernel > LBM_KERNEL_PREFETCH)
     return fail(nullptr, LBM_EINVAL, "unknown kernel choice %d", o.kernel);
+  if (!(o.mu >= 0.0) || !std::isfinite(o.mu)) return fail(nullptr, LBM_EINVAL, "mu must be >= 0");
   if (o.tma_stages != 0 && (o.tma_stages < 2 || o.tma_stages > 8))
     return fail(nullptr, LBM_EINVAL, "tma_stages must be 0 or 2..8 (got %d)", o.tma_stages);
   lbm_gfield gf{};
@@ -391,6 +393,8 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   p.gkind = gf.kind; p.gaxis = gf.wave_axis;
   for (int a = 0; a < 3; ++a) p.g0[a] = a < D ? gf.g0[a] : 0.0;
   p.omega_f = (float)p.omega;
+  p.mu = o.mu > 0.0 ? o.mu : 0.0;
+  p.mu_f = (float)p.mu;
   for (int a = 0; a < 3; ++a) p.g0_f[a] = (float)p.g0[a];
   p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
   if (wall != lbm::W_NONE) {

@@ -42,8 +42,10 @@ struct StepParams {
   float h_scale;      // FP16 codec scale s and 1/s
   float h_inv_scale;
   int* err;           // set to 1 by a kernel whose bounded wait ran out
+  double mu;          // > 0: constant dynamic viscosity, 1/omega = mu/(rho theta) + 1/2 per site
   // float copies for the float kernels (no FP64 conversion on their path)
   float omega_f;
+  float mu_f;
   float g0_f[3];
   const float* gtab_f;  // float copy of gtab (same layout)
 };
@@ -54,12 +56,14 @@ struct ParamsOf;
 template <>
 struct ParamsOf<double> {
   __device__ __forceinline__ static double omega(const StepParams& p) { return p.omega; }
+  __device__ __forceinline__ static double mu(const StepParams& p) { return p.mu; }
   __device__ __forceinline__ static double g0(const StepParams& p, int a) { return p.g0[a]; }
   __device__ __forceinline__ static double gtab(const StepParams& p, size_t k) { return __ldg(p.gtab + k); }
 };
 template <>
 struct ParamsOf<float> {
   __device__ __forceinline__ static float omega(const StepParams& p) { return p.omega_f; }
+  __device__ __forceinline__ static float mu(const StepParams& p) { return p.mu_f; }
   __device__ __forceinline__ static float g0(const StepParams& p, int a) { return p.g0_f[a]; }
   __device__ __forceinline__ static float gtab(const StepParams& p, size_t k) { return __ldg(p.gtab_f + k); }
 };
@@ -97,6 +101,17 @@ __device__ __forceinline__ R imul(R v) {
   else if constexpr (K == 1) return v;
   else if constexpr (K == -1) return -v;
   else return R(K) * v;
+}
+
+// Relaxation rate 1/tau-hat at a site: the grid's constant, or with constant
+// dynamic viscosity mu (the paper's validation runs set tau = mu/(rho theta))
+// 1 / (mu / (rho theta) + 1/2) from the mid-point rho and theta.
+template <class R>
+struct ParamsOf;
+template <class R>
+__device__ __forceinline__ R site_omega(const StepParams& p, R rho, R theta) {
+  if (p.mu > 0.0) return R(1) / (ParamsOf<R>::mu(p) / (rho * theta) + R(0.5));
+  return ParamsOf<R>::omega(p);
 }
 
 // Products by the quadrature constants (w_i, c, c^2, |xi|^2).  In float the

@@ -191,7 +191,7 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
                    R(1.0 / D) + g2 * R(0.25 / D);
   const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const R gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
-  const R om = ParamsOf<R>::omega(p);
+  const R om = site_omega<R>(p, rho, R(1) + Th);
   const R om1 = R(1) - om;
   const R hom1 = R(0.5) * om1;
   const R kf = R(1) - R(0.5) * om;
@@ -438,9 +438,10 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
     for (int a = 0; a < D; ++a) u[a * N + site] = m.u[a];
   if (q) {
     double qq[3];
-    if (force_order == 0) heat_flux<L, 0>(d, m, p.omega, qq);
-    else if (force_order == 1) heat_flux<L, 1>(d, m, p.omega, qq);
-    else heat_flux<L, 2>(d, m, p.omega, qq);
+    const double om = site_omega<double>(p, m.rho, 1.0 + m.theta_m1);
+    if (force_order == 0) heat_flux<L, 0>(d, m, om, qq);
+    else if (force_order == 1) heat_flux<L, 1>(d, m, om, qq);
+    else heat_flux<L, 2>(d, m, om, qq);
     for (int a = 0; a < D; ++a) q[a * N + site] = qq[a];
   }
 }

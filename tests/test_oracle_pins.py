@@ -442,3 +442,30 @@ def test_thermal_wall_conduction():
     dTdy = slope / sim.c  # lattice spacing is c
     lam = (2 + 2) / 2 * p[bulk].mean() * (tau - 0.5)
     np.testing.assert_allclose(qy[bulk], -lam * dTdy, rtol=1e-2)
+
+
+# ------------------- constant dynamic viscosity: nu = mu / rho at any theta
+@pytest.mark.parametrize("rho0,theta0", [(2.0, 1.0), (1.5, 1.2)])
+def test_constant_mu_kolmogorov(rho0, theta0):
+    """With tau = mu / (rho theta) (the paper's validation runs, Sec. 3.1) the
+    shear viscosity is mu = p tau = rho theta tau whatever the local state, so
+    a Kolmogorov flow at density rho0 and temperature theta0 follows the
+    transient closed form with nu = mu / rho0 (independent of theta0);
+    tau-hat = mu / (rho theta) + 1/2 per site."""
+    n, mu, g0, steps = 64, 0.6, 1e-5, 1000
+    w = W.kolmogorov(nx=n, ny=n, tau=0.8, g0=g0, rho_noise=0.0, T_amp=0.0)
+    g = W.g_field_array(w["lattice"], w["shape"], w["g"])
+    sim = oracle.OracleSim(oracle.D2Q37, n, n, 1, 0.8, g, mu=mu)
+    sim.init(rho0 * np.asarray(w["rho"]), w["u"], theta0 * np.ones(n * n))
+    sim.step(steps)
+    rho, u, T, _ = sim.moments()
+    s = np.sin(2 * np.pi * np.arange(n) / n)
+    amp = np.mean(u[0].reshape(n, n), axis=1) @ s / (s @ s)
+    L = n * sim.c
+    k = 2 * np.pi / L
+    nu = mu / rho0
+    ref = g0 / (nu * k * k) * (1 - np.exp(-nu * k * k * steps))
+    assert abs(amp / ref - 1) < 5e-3, (amp, ref)
+    # rho and theta move by O(u^2) only (pressure and viscous heating)
+    u2 = float(np.max(u[0] ** 2))
+    assert np.max(np.abs(rho / rho0 - 1)) < u2 and np.max(np.abs(T / theta0 - 1)) < u2

@@ -137,6 +137,33 @@ def test_reduced_precision_white_noise(case, precision):
     check_fields(sim, ref, w, 1e-5 if precision == 1 else 2e-3)
 
 
+MU_CASES = [CASES[0], CASES[4], CASES[5], CASES[6]]
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("case", MU_CASES, ids=[c[0] for c in MU_CASES])
+def test_constant_mu_parity(case, precision):
+    """Constant dynamic viscosity: tau-hat = mu / (rho theta) + 1/2 per site
+    from the mid-point state, in the update and the heat-flux diagnostic."""
+    w = make_case(case, precision)
+    w["mu"] = 0.25
+    w["tau"] = 5.0  # unused with mu > 0: a wrong path would show
+    sim, ref = run_both(w, 12)
+    check_fields(sim, ref, w, TOL[precision])
+    if precision == 0:
+        fg = sim.populations()
+        fo = ref.pulled()[perm_to_oracle(w["lattice"])]
+        assert np.max(np.abs(fg - fo)) < 1e-14
+
+
+def test_constant_mu_rejects_negative():
+    w = workload(0, (16, 8, 1))
+    w["mu"] = -1.0
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Sim(w)
+    assert ei.value.status == lbm.LBM_EINVAL
+
+
 @pytest.mark.parametrize("lat,shape,bc", [(0, (21, 13, 1), (0, 0, 0)), (0, (19, 10, 1), (0, 1, 0)),
                                           (1, (6, 5, 7), (0, 0, 1))])
 @pytest.mark.parametrize("precision", [0, 1, 2])
