@@ -96,8 +96,14 @@ typedef struct {
   int force_order;   /* the paper's N in Eq. F: force terms n <= N+1.
                         0: n = 1 only; 1: n <= 2 (the Guo scheme, Sec. 2);
                         2: n <= 3, the third-moment term of Eq. fi (default)  */
-  int include_sigma; /* deviatoric-stress terms of Eq. fi: must be 0 (the
-                        paper neglects them, Sec. 2 and 3.1)                 */
+  int include_sigma; /* 1: keep the deviatoric stress in the force's second
+                        coefficient, a^(2) = a^(2)_0 - sigma-bar (Eq. f2, the
+                        sigma terms of Eq. fi), with sigma-bar = -(1 - 1/(2
+                        tau-hat)) sum_i (f~_i - f0_i)(xi_i - u)(xi_i - u).
+                        Acts at force_order 2 only (it enters the n = 3 term);
+                        runs in the plain step kernel (LBM_KERNEL_TMA and
+                        LBM_KERNEL_PREFETCH are rejected) and not in batches.
+                        0: neglected, as in the paper's runs (default)       */
   int bc[3];         /* per axis: LBM_PERIODIC | LBM_BOUNCE_BACK | LBM_THERMAL_WALL */
   double T_lo[3];    /* wall temperature at x_a = -1/2 (THERMAL_WALL)         */
   double T_hi[3];    /* wall temperature at x_a = n_a - 1/2                   */

@@ -311,10 +311,11 @@ def lbm_batch_destroy(b):
 # ------------------------------------------------------------ convenience
 def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
             T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0, kernel=LBM_KERNEL_AUTO,
-            tma_stages=0, mu=0.0):
+            tma_stages=0, mu=0.0, include_sigma=False):
     o = lbm_default_options()
     o.precision = precision
     o.force_order = force_order
+    o.include_sigma = int(bool(include_sigma))
     for a in range(3):
         o.bc[a] = bc[a]
         o.T_lo[a] = T_lo[a]
@@ -345,7 +346,8 @@ class Sim:
         prec = w.get("precision", LBM_FP64) if precision is None else precision
         self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
                            w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
-                           block_x, graph_steps, kernel, tma_stages, w.get("mu", 0.0))
+                           block_x, graph_steps, kernel, tma_stages, w.get("mu", 0.0),
+                           w.get("include_sigma", False))
         g = w.get("g")
         self._gfield = g
         self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)

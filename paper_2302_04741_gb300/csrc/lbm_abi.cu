@@ -197,7 +197,7 @@ bool setup_step_kernel(lbm_ctx* c, std::string* why) {
       return false;
     }
     int bps = 0, nsm = 0;
-    cudaError_t e = c->ops->async_occupancy(c->opt.force_order, c->opt.block_x, &bps);
+    cudaError_t e = c->ops->async_occupancy(c->fo, c->opt.block_x, &bps);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess || bps < 1) {
       cudaGetLastError();
@@ -239,13 +239,13 @@ bool setup_step_kernel(lbm_ctx* c, std::string* why) {
 int launch_one_step(lbm_ctx* c) {
   cudaError_t e;
   if (c->use_tma)
-    e = c->ops->step_tma(c->opt.precision, c->opt.force_order, &c->tmap[c->cur], c->f[c->cur],
+    e = c->ops->step_tma(c->opt.precision, c->fo, &c->tmap[c->cur], c->f[c->cur],
                          c->f[c->cur ^ 1], c->p, c->tma_grid, c->tma_stages, c->stream);
   else if (c->use_async)
-    e = c->ops->step_async(c->opt.force_order, c->f[c->cur], c->f[c->cur ^ 1], c->p, c->async_grid,
+    e = c->ops->step_async(c->fo, c->f[c->cur], c->f[c->cur ^ 1], c->p, c->async_grid,
                            c->opt.block_x, c->stream);
   else
-    e = c->ops->step(c->opt.precision, c->opt.force_order, c->f[c->cur], c->f[c->cur ^ 1], c->p,
+    e = c->ops->step(c->opt.precision, c->fo, c->f[c->cur], c->f[c->cur ^ 1], c->p,
                      c->opt.block_x, c->stream);
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   c->cur ^= 1;
@@ -323,7 +323,9 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     return fail(nullptr, LBM_EINVAL, "unknown precision %d", o.precision);
   if (o.force_order < 0 || o.force_order > 2)
     return fail(nullptr, LBM_EINVAL, "force_order must be 0, 1 or 2 (got %d)", o.force_order);
-  if (o.include_sigma) return fail(nullptr, LBM_EINVAL, "include_sigma is not supported");
+  if (o.include_sigma && o.force_order == 2 &&
+      (o.kernel == LBM_KERNEL_TMA || o.kernel == LBM_KERNEL_PREFETCH))
+    return fail(nullptr, LBM_EINVAL, "the sigma-bar terms run in the plain step kernel only");
   const int n[3] = {nx, ny, nz};
   int wall = lbm::W_NONE;
   for (int a = 0; a < 3; ++a) {
@@ -359,6 +361,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   if (!c) return fail(nullptr, LBM_ENOMEM, "out of host memory");
   c->lat = lat; c->D = D; c->Q = ops->Q; c->nx = nx; c->ny = ny; c->nz = nz; c->N = (int)N;
   c->tau = tau; c->opt = o; c->ops = ops;
+  c->fo = o.include_sigma && o.force_order == 2 ? 3 : o.force_order;
   c->elem = o.precision == LBM_FP64 ? 8 : (o.precision == LBM_FP32_SHIFTED ? 4 : 2);
   cudaGetDevice(&c->device);
   auto bail = [&](int rc) {
@@ -393,8 +396,9 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   p.gkind = gf.kind; p.gaxis = gf.wave_axis;
   for (int a = 0; a < 3; ++a) p.g0[a] = a < D ? gf.g0[a] : 0.0;
   p.omega_f = (float)p.omega;
-  p.mu = o.mu > 0.0 ? o.mu : 0.0;
-  p.mu_f = (float)p.mu;
+  p.mu_f = (float)o.mu;
+  p.mu = p.mu_f > 0.0f ? o.mu : 0.0;  // the same switch in both precisions
+  if (p.mu == 0.0) p.mu_f = 0.0f;
   for (int a = 0; a < 3; ++a) p.g0_f[a] = (float)p.g0[a];
   p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
   if (wall != lbm::W_NONE) {
@@ -564,7 +568,7 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* T, double* q) {
     t += cnt[k];
   }
   LBM_CUDA(c, c->ops->moments(c->opt.precision, c->f[c->cur], dst[0], dst[1], dst[2], dst[3],
-                              c->opt.force_order, c->p, c->stream));
+                              c->fo, c->p, c->stream));
   for (int k = 0; k < 4; ++k)
     if (outs[k] && dst[k] != outs[k])
       LBM_CUDA(c, cudaMemcpyAsync(outs[k], dst[k], cnt[k] * sizeof(double), cudaMemcpyDefault, c->stream));

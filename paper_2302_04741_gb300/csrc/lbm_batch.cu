@@ -199,7 +199,7 @@ int lbm_batch_add(lbm_batch* b, lbm_ctx* c) {
   if (!b || !c) return bfail(b, LBM_EINVAL, "batch and ctx are required");
   if (c->batch) return bfail(b, LBM_ESTATE, "ctx is already in a batch");
   if (!c->initialised) return bfail(b, LBM_ESTATE, "ctx is not initialised");
-  if (c->lat != b->lat || c->opt.precision != b->precision || c->opt.force_order != b->force_order)
+  if (c->lat != b->lat || c->opt.precision != b->precision || c->fo != b->force_order)
     return bfail(b, LBM_EINVAL, "ctx lattice / precision / force order differ from the batch");
   if (c->stream != b->stream) return bfail(b, LBM_EINVAL, "ctx must use the batch's stream");
   if (c->device != b->device) return bfail(b, LBM_EINVAL, "ctx lives on another device");

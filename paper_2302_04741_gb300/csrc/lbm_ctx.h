@@ -17,6 +17,8 @@ struct lbm_ctx {
   int N = 0;
   double tau = 0.0;
   lbm_options opt{};
+  int fo = 2;                  // kernel force-order code: opt.force_order, or 3 for
+                               // order 2 with the sigma-bar terms
   const lbm::LatticeOps* ops = nullptr;
   size_t elem = 0;             // bytes per stored population value
   void* f[2] = {nullptr, nullptr};

@@ -110,7 +110,8 @@ template <class R>
 struct ParamsOf;
 template <class R>
 __device__ __forceinline__ R site_omega(const StepParams& p, R rho, R theta) {
-  if (p.mu > 0.0) return R(1) / (ParamsOf<R>::mu(p) / (rho * theta) + R(0.5));
+  const R mu = ParamsOf<R>::mu(p);
+  if (mu > R(0)) return R(1) / (mu / (rho * theta) + R(0.5));
   return ParamsOf<R>::omega(p);
 }
 
@@ -376,6 +377,87 @@ template <class L, int FO, class R>
 __device__ __forceinline__ void rest_terms(const MidState<L, R>& m, R& E, R& Fe) {
   E = m.A0[0];
   Fe = FO >= 1 ? -m.gu : R(0);
+}
+
+// ------------------------------------------- sigma-bar terms (force order 2)
+// Keeping the deviatoric stress in the second Hermite coefficient of the
+// force, a^(2) = a^(2)_0 - sigma-bar (Eq. f2), adds to the n = 3 term of
+// Eq. F (w_i / 2 times g a^(2) : H^(3)) the odd part
+//   -(w_i / 2) [(g.xi)(xi.sigma.xi - tr sigma) - 2 g.sigma.xi],
+// sigma-bar = -(1 - om/2) S (the reading of Eq. sigma used throughout) with
+//   S = sum_i f~_i (xi_i - u)(xi_i - u) - rho theta delta
+//     = c^2 P - (drho + rho Th) delta - rho u u + rho (u g + g u) / 2,
+// P_ab = sum_i d_i e_ia e_ib over the deviations (sum_i w_i xi xi = delta),
+// u the mid-point velocity, u~ = u - g/2.  tr S vanishes identically because
+// theta is taken from the same f~, so the trace term is dropped.
+// S is stored as (xx, yy, zz, xy, xz, yz); in 2-D the z entries are zero.
+template <class L, class R>
+__device__ __forceinline__ void stress_tensor(const R (&d)[L::Q], R drho, R rho, R Th,
+                                              const R (&u)[3], const R (&g)[3], R (&S)[6]) {
+  constexpr int NP = (L::Q - 1) / 2;
+  R P0 = R(0), P1 = R(0), P2 = R(0), P3 = R(0), P4 = R(0), P5 = R(0);
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    constexpr int ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
+    const R s = d[ip] + d[im];
+    P0 = mac<ex * ex>(s, P0);
+    P1 = mac<ey * ey>(s, P1);
+    P3 = mac<ex * ey>(s, P3);
+    if constexpr (L::D == 3) {
+      P2 = mac<ez * ez>(s, P2);
+      P4 = mac<ex * ez>(s, P4);
+      P5 = mac<ey * ez>(s, P5);
+    }
+  });
+  const R iso = fma(rho, Th, drho);
+  const R hr = R(0.5) * rho;
+  // -rho u_a u_b + rho (u_a g_b + g_a u_b) / 2
+  auto conv = [&](int a, int b) { return hr * (u[a] * (g[b] - u[b]) + u[b] * (g[a] - u[a])); };
+  S[0] = mul_c2<L, R>(P0) - iso + conv(0, 0);
+  S[1] = mul_c2<L, R>(P1) - iso + conv(1, 1);
+  S[3] = mul_c2<L, R>(P3) + conv(0, 1);
+  if constexpr (L::D == 3) {
+    S[2] = mul_c2<L, R>(P2) - iso + conv(2, 2);
+    S[4] = mul_c2<L, R>(P4) + conv(0, 2);
+    S[5] = mul_c2<L, R>(P5) + conv(1, 2);
+  } else {
+    S[2] = S[4] = S[5] = R(0);
+  }
+}
+
+// Per-site factors of the odd term k [(g.xi)(xi.S.xi) - 2 (S g).xi] in
+// lattice vectors: gs = k c^3 g, hs = 2 k c S g.
+template <class R>
+struct StressTerms {
+  R gs[3], S[6], hs[3];
+};
+
+template <class L, class R>
+__device__ __forceinline__ StressTerms<R> stress_terms(const R (&S)[6], const R (&g)[3], R k) {
+  StressTerms<R> st;
+  const R kc3 = k * R(L::c * L::c2), kc2 = R(2) * k * R(L::c);
+  const R Sg0 = S[0] * g[0] + S[3] * g[1] + S[4] * g[2];
+  const R Sg1 = S[3] * g[0] + S[1] * g[1] + S[5] * g[2];
+  const R Sg2 = S[4] * g[0] + S[5] * g[1] + S[2] * g[2];
+  st.gs[0] = kc3 * g[0]; st.gs[1] = kc3 * g[1]; st.gs[2] = kc3 * g[2];
+  st.hs[0] = kc2 * Sg0; st.hs[1] = kc2 * Sg1; st.hs[2] = kc2 * Sg2;
+  for (int a = 0; a < 6; ++a) st.S[a] = S[a];
+  return st;
+}
+
+// The odd stress term of the pair (e, -e) of direction IP (value for +e).
+template <class L, int IP, class R>
+__device__ __forceinline__ R stress_pair(const StressTerms<R>& st) {
+  constexpr int ex = L::E(IP, 0), ey = L::E(IP, 1), ez = L::E(IP, 2);
+  R eSe = imul<ex * ex>(st.S[0]);
+  eSe = mac<ey * ey>(st.S[1], eSe);
+  eSe = mac<2 * ex * ey>(st.S[3], eSe);
+  if constexpr (L::D == 3) {
+    eSe = mac<ez * ez>(st.S[2], eSe);
+    eSe = mac<2 * ex * ez>(st.S[4], eSe);
+    eSe = mac<2 * ey * ez>(st.S[5], eSe);
+  }
+  return fma(edot<L, IP>(st.gs), eSe, -edot<L, IP>(st.hs));
 }
 
 }  // namespace lbm

@@ -240,6 +240,14 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   });
   const R P4 = L::NEQ >= 4 ? rom * R(1.0 / 24.0) : R(0);
   const R Q3 = rom * R(1.0 / 6.0);
+  // sigma-bar terms (FO 3 = force order 2 with sigma-bar): the odd part gains
+  // rho k dF'_i = (k^2 / 2) [(g.xi)(xi.S.xi) - 2 (S g).xi]
+  StressTerms<R> st;
+  if constexpr (FO == 3) {
+    R S[6];
+    stress_tensor<L, R>(d, r.drho, rho, Th, u, g, S);
+    st = stress_terms<L, R>(S, g, R(0.5) * kf * kf);
+  }
   // rest particle: t = s' = 0
   typename C::T* __restrict__ fo = fout + site;
   fo[0] = C::template encode<L, 0>(fma(d[0], om1, mul_w<L, 0>(P0[0])), p);
@@ -257,6 +265,7 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
     } else {
       od_in = od_in + edot<L, ip>(cs);
     }
+    if constexpr (FO == 3) od_in += stress_pair<L, ip, R>(st);
     const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip>(ev_in));
     const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip>(od_in));
     fo[ip * N] = C::template encode<L, ip>(ev + od, p);
@@ -384,12 +393,20 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
 // Physical rho, u, T and heat flux q in double (the FP64 diagnostic):
 // q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2) |xi_i - u|^2 (xi_i - u)
 // where f~_i - f0_i + F_i/2 = d_i - w_i [drho + rho (p_i - F'_i/2)].
+// With sigma-bar (FO 3) the odd force part gains (k / (2 rho)) [(g.xi)(xi.S.xi)
+// - 2 (S g).xi], k = 1 - om/2 (see stress_tensor).
 template <class L, int FO>
 __device__ __forceinline__ void heat_flux(const double (&d)[L::Q], const MidState<L, double>& m,
-                                          double omega, double (&q)[3]) {
+                                          const double (&g)[3], double omega, double (&q)[3]) {
   constexpr int NP = (L::Q - 1) / 2;
   const double c = L::c;
   q[0] = q[1] = q[2] = 0.0;
+  StressTerms<double> st;
+  if constexpr (FO == 3) {
+    double S[6];
+    stress_tensor<L, double>(d, m.drho, m.rho, m.theta_m1, m.u, g, S);
+    st = stress_terms<L, double>(S, g, 0.5 * (1.0 - 0.5 * omega) / m.rho);
+  }
   auto add = [&](double fneq, double e0, double e1, double e2) {
     const double c0 = c * e0 - m.u[0], c1 = c * e1 - m.u[1], c2 = c * e2 - m.u[2];
     const double w = fneq * (c0 * c0 + c1 * c1 + c2 * c2);
@@ -406,6 +423,7 @@ __device__ __forceinline__ void heat_flux(const double (&d)[L::Q], const MidStat
     constexpr int ip = 2 * K + 1, im = ip + 1;
     double E, O, Fe, Fo;
     pair_terms<L, FO, ip, double>(m, E, O, Fe, Fo);
+    if constexpr (FO == 3) Fo += stress_pair<L, ip, double>(st);
     constexpr double ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
     add(d[ip] - L::W(ip) * fma(m.rho, (E + O) - 0.5 * (Fe + Fo), m.drho), ex, ey, ez);
     add(d[im] - L::W(im) * fma(m.rho, (E - O) - 0.5 * (Fe - Fo), m.drho), -ex, -ey, -ez);
@@ -439,9 +457,10 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
   if (q) {
     double qq[3];
     const double om = site_omega<double>(p, m.rho, 1.0 + m.theta_m1);
-    if (force_order == 0) heat_flux<L, 0>(d, m, om, qq);
-    else if (force_order == 1) heat_flux<L, 1>(d, m, om, qq);
-    else heat_flux<L, 2>(d, m, om, qq);
+    if (force_order == 0) heat_flux<L, 0>(d, m, g, om, qq);
+    else if (force_order == 1) heat_flux<L, 1>(d, m, g, om, qq);
+    else if (force_order == 2) heat_flux<L, 2>(d, m, g, om, qq);
+    else heat_flux<L, 3>(d, m, g, om, qq);
     for (int a = 0; a < D; ++a) q[a * N + site] = qq[a];
   }
 }

@@ -51,13 +51,14 @@ struct Ops {
                           cudaStream_t s) {
     const dim3 g = row_grid(p, bx), b(bx);
 #define LBM_STEP_CASE(PP, FF)                                                            \
-  case PP * 3 + FF:                                                                      \
+  case PP * 4 + FF:                                                                      \
     k_step<L, PP, FF><<<g, b, 0, s>>>((const T<PP>*)fin, (T<PP>*)fout, p);               \
     break;
-    switch (P * 3 + FO) {
-      LBM_STEP_CASE(0, 0) LBM_STEP_CASE(0, 1) LBM_STEP_CASE(0, 2)
-      LBM_STEP_CASE(1, 0) LBM_STEP_CASE(1, 1) LBM_STEP_CASE(1, 2)
-      LBM_STEP_CASE(2, 0) LBM_STEP_CASE(2, 1) LBM_STEP_CASE(2, 2)
+    // FO 3: force order 2 with the sigma-bar terms (plain kernel only)
+    switch (P * 4 + FO) {
+      LBM_STEP_CASE(0, 0) LBM_STEP_CASE(0, 1) LBM_STEP_CASE(0, 2) LBM_STEP_CASE(0, 3)
+      LBM_STEP_CASE(1, 0) LBM_STEP_CASE(1, 1) LBM_STEP_CASE(1, 2) LBM_STEP_CASE(1, 3)
+      LBM_STEP_CASE(2, 0) LBM_STEP_CASE(2, 1) LBM_STEP_CASE(2, 2) LBM_STEP_CASE(2, 3)
       default: return cudaErrorInvalidValue;
     }
 #undef LBM_STEP_CASE

@@ -26,7 +26,8 @@ def oracle_sim(w):
     g = W.g_field_array(w["lattice"], w["shape"], w["g"])
     s = oracle.OracleSim(w["lattice"], *w["shape"], w["tau"], g, force_order=w.get("force_order", 2),
                          bc=w.get("bc", (0, 0, 0)), T_lo=w.get("T_lo", (1, 1, 1)),
-                         T_hi=w.get("T_hi", (1, 1, 1)), mu=w.get("mu", 0.0))
+                         T_hi=w.get("T_hi", (1, 1, 1)), mu=w.get("mu", 0.0),
+                         include_sigma=w.get("include_sigma", False))
     s.init(w["rho"], w["u"], w["T"])
     return s
 

@@ -248,14 +248,15 @@ def pulled_sums(sim):
 
 
 @pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (7, 5, 1)), (oracle.D3Q39, (4, 5, 3))])
-@pytest.mark.parametrize("order", [1, 2])
-def test_budgets_per_step(lat, shape, order):
+@pytest.mark.parametrize("order,sigma", [(1, False), (2, False), (2, True)])
+def test_budgets_per_step(lat, shape, order, sigma):
     """(c): per step, total momentum changes by exactly sum rho g and total
-    energy sum f xi^2 by sum 2 rho g.u (mid-point u); mass is unchanged."""
+    energy sum f xi^2 by sum 2 rho g.u (mid-point u); mass is unchanged.  The
+    sigma-bar terms (odd, orthogonal to 1, xi and xi^2) change none of them."""
     D = W.dims(lat)
     N = shape[0] * shape[1] * shape[2]
     g = 1e-3 * (W.uniform(7, 14, D * N).reshape(D, N) - 0.5)
-    sim = make_sim(lat, shape, 0.7, g, order=order)
+    sim = make_sim(lat, shape, 0.7, g, order=order, sigma=sigma)
     sim.init(*smooth_random_state(lat, shape, 3))
     sim.step(2)
     for _ in range(3):
@@ -466,6 +467,34 @@ def test_constant_mu_kolmogorov(rho0, theta0):
     nu = mu / rho0
     ref = g0 / (nu * k * k) * (1 - np.exp(-nu * k * k * steps))
     assert abs(amp / ref - 1) < 5e-3, (amp, ref)
+    # sigma-bar is the Newtonian viscous stress mu (du_x/dy) with mu given
+    # (Chapman-Enskog of Eq. lbm: sigma-bar = (tau-hat - 1/2) rho theta (grad u
+    # + grad u^T) for a solenoidal flow); u_x = A sin(k y) gives A k cos(k y)
+    sig = sim.moments(with_sigma=True)[4]
+    cs = np.cos(2 * np.pi * np.arange(n) / n)
+    B = np.mean(sig[0, 1].reshape(n, n), axis=1) @ cs / (cs @ cs)
+    assert abs(B / (mu * amp * k) - 1) < 5e-3, (B, mu * amp * k)
+    np.testing.assert_allclose(sig[0, 1], sig[1, 0], rtol=0, atol=1e-18)
     # rho and theta move by O(u^2) only (pressure and viscous heating)
     u2 = float(np.max(u[0] ** 2))
     assert np.max(np.abs(rho / rho0 - 1)) < u2 and np.max(np.abs(T / theta0 - 1)) < u2
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (6, 5, 1)), (oracle.D3Q39, (4, 3, 5))])
+def test_sigma_bar_is_traceless(lat, shape):
+    """sigma-bar = -(1 - 1/(2 tau-hat)) sum (f~ - f0)(xi - u)(xi - u) has zero
+    trace at any state: theta is defined from the same pulled f~ (Eq. rut1 with
+    the mid-point correction), so sum (f~ - f0) |xi - u|^2 = 0."""
+    D = W.dims(lat)
+    N = shape[0] * shape[1] * shape[2]
+    g = 1e-3 * (W.uniform(9, 14, D * N).reshape(D, N) - 0.5)
+    sim = make_sim(lat, shape, 0.7, g, sigma=True)
+    sim.init(*smooth_random_state(lat, shape, 4))
+    rng = np.random.default_rng(3)
+    f = sim.get_state()
+    sim.set_state(f * (1 + 0.05 * rng.standard_normal(f.shape)))
+    sig = sim.moments(with_sigma=True)[4]
+    tr = np.einsum("aan->n", sig)
+    scale = np.max(np.abs(sig))
+    assert scale > 1e-4
+    assert np.max(np.abs(tr)) < 1e-13 * max(scale, 1.0)

@@ -164,6 +164,61 @@ def test_constant_mu_rejects_negative():
     assert ei.value.status == lbm.LBM_EINVAL
 
 
+SIGMA_CASES = [c for c in CASES if c[4] == 2]
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("case", SIGMA_CASES, ids=[c[0] for c in SIGMA_CASES])
+def test_sigma_bar_parity(case, precision):
+    """Force order 2 with the sigma-bar terms (a^(2) = a^(2)_0 - sigma-bar in
+    the n = 3 force term).  |g| ~ 5e-4 with the sheared smooth state makes the
+    terms change the populations by far more than the FP64 tolerance."""
+    w = make_case(case, precision)
+    D = W.dims(w["lattice"])
+    w["g"] = {"kind": W.G_UNIFORM, "g0": (4e-4, -3e-4, 2e-4)[:D] + (0.0,) * (3 - D)}
+    w["include_sigma"] = True
+    sim, ref = run_both(w, 12)
+    check_fields(sim, ref, w, TOL[precision])
+    if precision == 0:
+        perm = perm_to_oracle(w["lattice"])
+        fo = ref.pulled()[perm]
+        assert np.max(np.abs(sim.populations() - fo)) < 1e-14
+        plain = oracle_sim(dict(w, include_sigma=False))
+        plain.step(12)
+        assert np.max(np.abs(plain.pulled()[perm] - fo)) > 1e-11
+
+
+def test_sigma_bar_with_constant_mu():
+    w = make_case(CASES[4], 0)
+    w["g"] = {"kind": W.G_UNIFORM, "g0": (3e-4, -5e-4, 0.0)}
+    w["include_sigma"] = True
+    w["mu"] = 0.2
+    sim, ref = run_both(w, 12)
+    check_fields(sim, ref, w, TOL[0])
+    fo = ref.pulled()[perm_to_oracle(w["lattice"])]
+    assert np.max(np.abs(sim.populations() - fo)) < 1e-14
+
+
+def test_sigma_bar_needs_plain_kernel():
+    w = workload(0, (64, 12, 1), precision=1)
+    w["include_sigma"] = True
+    for kern in (lbm.LBM_KERNEL_TMA, lbm.LBM_KERNEL_PREFETCH):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.Sim(w, kernel=kern)
+        assert ei.value.status == lbm.LBM_EINVAL
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    sim = lbm.Sim(w, stream=stream.cuda_stream).init()
+    b = lbm.lbm_batch_create(0, 1, 2, stream.cuda_stream, 2)
+    try:
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_batch_add(b, sim.ctx)
+        assert ei.value.status == lbm.LBM_EINVAL and "force order" in str(ei.value)
+    finally:
+        lbm.lbm_batch_destroy(b)
+        sim.close()
+
+
 @pytest.mark.parametrize("lat,shape,bc", [(0, (21, 13, 1), (0, 0, 0)), (0, (19, 10, 1), (0, 1, 0)),
                                           (1, (6, 5, 7), (0, 0, 1))])
 @pytest.mark.parametrize("precision", [0, 1, 2])
