@@ -178,7 +178,8 @@ def test_sigma_bar_parity(case, precision):
     w["g"] = {"kind": W.G_UNIFORM, "g0": (4e-4, -3e-4, 2e-4)[:D] + (0.0,) * (3 - D)}
     w["include_sigma"] = True
     sim, ref = run_both(w, 12)
-    check_fields(sim, ref, w, TOL[precision])
+    # FP16: at this |g| the D3Q39 heat flux sits at the codec's 1e-3 floor
+    check_fields(sim, ref, w, 2e-3 if precision == 2 else TOL[precision])
     if precision == 0:
         perm = perm_to_oracle(w["lattice"])
         fo = ref.pulled()[perm]
