@@ -133,6 +133,48 @@ def rayleigh_benard(nx=1024, ny=512, nz=1, lattice=D2Q37, tau=0.6, g=-1e-5, T_bo
                 name=f"rayleigh_benard_{nx}x{ny}" + (f"x{nz}" if D == 3 else ""))
 
 
+# Lattice constant of the D2Q37 rule as the paper prints it (Sec. 3): the
+# lattice spacing in units of the reference thermal speed.
+C_D2Q37 = 1.196979770393
+
+
+def poiseuille_parameters(theta_b, theta_t, Uc=1.5, Re=1800.0, Ly=150, Pr=1.0,
+                          gy_over_gx=-50.0, rho0=1.0, c=C_D2Q37, D=2):
+    """Parameters of the compressible Poiseuille validation case (Sec. 3.1):
+    channel height H = L_y c, dynamic viscosity mu = rho0 U_c H / Re,
+    conductivity lambda = c_p mu / Pr with c_p = (D + 2) / 2, and g_x from the
+    definition U_c = rho0 g_x H^2 / (8 mu), i.e. g_x = 8 U_c^2 / (Re H) (the
+    printed U_c^2 / (Re H) lacks the factor 8 this definition implies);
+    g_y = (g_y / g_x) g_x points down."""
+    H = Ly * c
+    mu = rho0 * Uc * H / Re
+    lam = (D + 2) / 2.0 * mu / Pr
+    gx = 8.0 * Uc * Uc / (Re * H)
+    return dict(H=H, mu=mu, lam=lam, gx=gx, gy=gy_over_gx * gx, rho0=rho0, theta_b=theta_b,
+                theta_t=theta_t, Uc=Uc, Re=Re, Ly=Ly)
+
+
+def poiseuille(theta_b=1.0, theta_t=1.1, force_order=2, include_sigma=False, Lx=3, Ly=150,
+               precision=FP64, **kw):
+    """Compressible Poiseuille flow under cross gravity on an L_x x L_y D2Q37
+    lattice (Sec. 3.1): thermal walls at y = -1/2 and L_y - 1/2 (theta_b below,
+    theta_t above, no slip), periodic in x, uniform g = (g_x, g_y), constant mu
+    (tau = mu / (rho theta) per site).  Starts from rest at rho = rho0 with theta
+    linear between the wall values."""
+    prm = poiseuille_parameters(theta_b, theta_t, Ly=Ly, **kw)
+    shape = (Lx, Ly, 1)
+    N = Lx * Ly
+    _, yy, _ = _coords(shape)
+    T = theta_b + (theta_t - theta_b) * (yy + 0.5) / Ly
+    return dict(lattice=D2Q37, shape=shape, tau=1.0, mu=prm["mu"], precision=precision,
+                force_order=force_order, include_sigma=include_sigma,
+                bc=(PERIODIC, THERMAL_WALL, PERIODIC), T_lo=(1.0, theta_b, 1.0),
+                T_hi=(1.0, theta_t, 1.0), g={"kind": G_UNIFORM, "g0": (prm["gx"], prm["gy"], 0.0)},
+                rho=np.full(N, prm["rho0"]), u=np.zeros((2, N)), T=T, params=prm,
+                name=f"poiseuille_{Lx}x{Ly}_theta{theta_b}-{theta_t}_N{force_order}"
+                     + ("_sigma" if include_sigma else ""))
+
+
 RAGGED_SIDES = (128, 192, 256, 384, 512)
 
 

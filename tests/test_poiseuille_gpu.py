@@ -1,0 +1,129 @@
+"""Compressible Poiseuille flow under cross gravity (Sec. 3.1, Fig. 1) on the
+GPU, against the finite-difference reference of Appendix A.
+
+Eight runs -- theta_b / theta_t = 1.0 / 1.1 and 0.7 / 1.4, force order N = 0,
+1, 2 and N = 2 with the sigma-bar terms -- step concurrently, one stream each,
+from rest to the steady state.  The reference is the FD solution on nodes that
+coincide with the lattice sites y_j = (j + 1/2) c, Richardson-extrapolated
+from 3601 and 7201 nodes (the forward pressure difference is first order).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2302_04741_gb300 as lbm
+from oracle import poiseuille_fd as fd
+from paper_2302_04741_gb300 import workloads as W
+from helpers import oracle_sim, perm_to_oracle
+
+pytestmark = pytest.mark.gpu
+
+THETAS = [(1.0, 1.1), (0.7, 1.4)]
+VARIANTS = [(0, False), (1, False), (2, False), (2, True)]
+CHUNK = 20000
+MAX_STEPS = 1_500_000
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2302_04741_gb300 import build
+    build.build()
+
+
+def fd_reference(prm, Ly):
+    """FD profiles at the lattice sites (Richardson from two resolutions)."""
+    out = []
+    for m in (12, 24):  # N - 1 = 300 m; site j sits on node (2 j + 1) m / 2
+        N = 2 * Ly * m + 1
+        y, rho, u, th, _ = fd.solve(N, prm["H"], prm["gx"], prm["gy"], prm["mu"], prm["lam"],
+                                    rho0=prm["rho0"], theta_b=prm["theta_b"],
+                                    theta_t=prm["theta_t"])
+        k = (2 * np.arange(Ly) + 1) * m // 2
+        out.append(np.stack([rho[k], u[k], th[k]]))
+    return 2 * out[1] - out[0]
+
+
+def profiles(sim, Ly):
+    rho, u, T, _ = sim.moments()
+    col = lambda a: a.reshape(Ly, -1).mean(axis=1)
+    return np.stack([col(rho), col(u[0]), col(T)]), float(np.max(np.abs(u[1])))
+
+
+@pytest.fixture(scope="module")
+def steady():
+    torch = pytest.importorskip("torch")
+    runs = []
+    for tb, tt in THETAS:
+        for fo, sig in VARIANTS:
+            w = W.poiseuille(tb, tt, force_order=fo, include_sigma=sig)
+            st = torch.cuda.Stream()
+            sim = lbm.Sim(w, stream=st.cuda_stream, block_x=32, graph_steps=100).init()
+            runs.append(dict(w=w, sim=sim, stream=st, prev=None, steps=0, done=False, change=None))
+    Ly = runs[0]["w"]["shape"][1]
+    while not all(r["done"] for r in runs):
+        live = [r for r in runs if not r["done"]]
+        for r in live:
+            r["sim"].step(CHUNK)
+        for r in live:
+            r["steps"] += CHUNK
+            prof, uy = profiles(r["sim"], Ly)
+            if r["prev"] is not None:
+                r["change"] = float(np.max(np.abs(prof - r["prev"])))
+                if r["change"] < 1e-9 or r["steps"] >= MAX_STEPS:
+                    r["done"] = True
+                    r["prof"], r["uy"] = prof, uy
+            r["prev"] = prof
+    table = {}
+    for r in runs:
+        prm = r["w"]["params"]
+        ref = fd_reference(prm, Ly)
+        err = np.abs(r["prof"] - ref)
+        key = (prm["theta_b"], prm["theta_t"], r["w"]["force_order"], r["w"]["include_sigma"])
+        table[key] = dict(rho=float(err[0].max()), u=float(err[1].max() / prm["Uc"]),
+                          theta=float(err[2].max()), steps=r["steps"], change=r["change"],
+                          uy=r["uy"], prof=r["prof"], ref=ref)
+        r["sim"].close()
+    print("\ntheta_b theta_t N sigma | max|d rho|  max|d u|/U_c  max|d theta| | steps")
+    for k, v in table.items():
+        print(f"{k[0]:.1f} {k[1]:.1f} {k[2]} {int(k[3])} | {v['rho']:.3e} {v['u']:.3e} "
+              f"{v['theta']:.3e} | {v['steps']} (last change {v['change']:.1e}, |u_y| {v['uy']:.1e})")
+    return table
+
+
+def test_runs_reach_steady_state(steady):
+    for k, v in steady.items():
+        assert v["change"] < 1e-9, (k, v["change"], v["steps"])
+        assert v["uy"] < 1e-6 * 1.5, (k, v["uy"])
+
+
+@pytest.mark.parametrize("thetas", THETAS)
+def test_third_order_force_matches_fd(steady, thetas):
+    """N = 2 reproduces the FD density, velocity and temperature."""
+    v = steady[(*thetas, 2, False)]
+    assert v["rho"] < 1e-2 and v["u"] < 1e-2 and v["theta"] < 1e-2, v
+
+
+@pytest.mark.parametrize("thetas", THETAS)
+def test_force_order_ranking(steady, thetas):
+    """Temperature error: N = 0 far off, N = 1 off at large temperature
+    variation, N = 2 closest; the sigma-bar terms change almost nothing."""
+    e = {fo: steady[(*thetas, fo, False)]["theta"] for fo in (0, 1, 2)}
+    assert e[0] > e[1] > e[2], e
+    with_sigma = steady[(*thetas, 2, True)]["prof"][2]
+    d = np.max(np.abs(with_sigma - steady[(*thetas, 2, False)]["prof"][2]))
+    assert d < 0.1 * e[2], (d, e[2])
+
+
+def test_poiseuille_step_parity_with_oracle():
+    """Twenty FP64 steps of the validation workload (constant mu, thermal
+    walls, strong cross gravity, sigma-bar terms) against the oracle."""
+    w = W.poiseuille(0.7, 1.4, force_order=2, include_sigma=True)
+    sim = lbm.Sim(w).init()
+    ref = oracle_sim(w)
+    sim.step(20)
+    ref.step(20)
+    perm = perm_to_oracle(w["lattice"])
+    np.testing.assert_allclose(sim.populations(), ref.pulled()[perm], rtol=0, atol=1e-14)
+    g, r = sim.moments(), ref.moments()
+    for a, b in zip(g[:3], r[:3]):
+        np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-15)
