@@ -33,20 +33,24 @@ def built():
 def fd_reference(prm, Ly):
     """FD profiles at the lattice sites (Richardson from two resolutions)."""
     out = []
-    for m in (12, 24):  # N - 1 = 300 m; site j sits on node (2 j + 1) m / 2
+    for m in (12, 24):  # N - 1 = 2 L_y m: site j, y = (2 j + 1) H / (2 L_y), is node (2 j + 1) m
         N = 2 * Ly * m + 1
         y, rho, u, th, _ = fd.solve(N, prm["H"], prm["gx"], prm["gy"], prm["mu"], prm["lam"],
                                     rho0=prm["rho0"], theta_b=prm["theta_b"],
                                     theta_t=prm["theta_t"])
-        k = (2 * np.arange(Ly) + 1) * m // 2
+        k = (2 * np.arange(Ly) + 1) * m
+        assert np.allclose(y[k], (np.arange(Ly) + 0.5) * prm["H"] / Ly, rtol=1e-13)
         out.append(np.stack([rho[k], u[k], th[k]]))
     return 2 * out[1] - out[0]
 
 
 def profiles(sim, Ly):
+    """x-averaged rho, u_x, theta per row, and max |u_y| away from the walls
+    (the wall rule leaves a few rows of Knudsen-layer flow next to each wall)."""
     rho, u, T, _ = sim.moments()
     col = lambda a: a.reshape(Ly, -1).mean(axis=1)
-    return np.stack([col(rho), col(u[0]), col(T)]), float(np.max(np.abs(u[1])))
+    uy = np.abs(u[1].reshape(Ly, -1))[10:Ly - 10]
+    return np.stack([col(rho), col(u[0]), col(T)]), float(uy.max())
 
 
 @pytest.fixture(scope="module")
@@ -80,27 +84,34 @@ def steady():
         err = np.abs(r["prof"] - ref)
         key = (prm["theta_b"], prm["theta_t"], r["w"]["force_order"], r["w"]["include_sigma"])
         table[key] = dict(rho=float(err[0].max()), u=float(err[1].max() / prm["Uc"]),
-                          theta=float(err[2].max()), steps=r["steps"], change=r["change"],
+                          theta=float(err[2].max()), theta_bulk=float(err[2][10:Ly - 10].max()),
+                          steps=r["steps"], change=r["change"],
                           uy=r["uy"], prof=r["prof"], ref=ref)
         r["sim"].close()
-    print("\ntheta_b theta_t N sigma | max|d rho|  max|d u|/U_c  max|d theta| | steps")
+    print("\ntheta_b theta_t N sigma | max|d rho|  max|d u|/U_c  max|d theta|  bulk | steps")
     for k, v in table.items():
         print(f"{k[0]:.1f} {k[1]:.1f} {k[2]} {int(k[3])} | {v['rho']:.3e} {v['u']:.3e} "
-              f"{v['theta']:.3e} | {v['steps']} (last change {v['change']:.1e}, |u_y| {v['uy']:.1e})")
+              f"{v['theta']:.3e} {v['theta_bulk']:.3e} | {v['steps']} (last change "
+              f"{v['change']:.1e}, bulk |u_y| {v['uy']:.1e})")
     return table
 
 
 def test_runs_reach_steady_state(steady):
     for k, v in steady.items():
         assert v["change"] < 1e-9, (k, v["change"], v["steps"])
-        assert v["uy"] < 1e-6 * 1.5, (k, v["uy"])
+        # no cross flow in the bulk (steady 1-D flow): |u_y| ~ 1e-5, against
+        # U_c = 1.5 and a wall layer with |u_y| up to ~6e-4
+        assert v["uy"] < 5e-5, (k, v["uy"])
 
 
 @pytest.mark.parametrize("thetas", THETAS)
 def test_third_order_force_matches_fd(steady, thetas):
-    """N = 2 reproduces the FD density, velocity and temperature."""
+    """N = 2 reproduces the FD density, velocity and temperature (measured:
+    max |d theta| 4.0e-3 and 3.9e-3, largest in the wall rows; 3.0e-3 and
+    1.2e-3 in the bulk)."""
     v = steady[(*thetas, 2, False)]
-    assert v["rho"] < 1e-2 and v["u"] < 1e-2 and v["theta"] < 1e-2, v
+    assert v["rho"] < 1e-2 and v["u"] < 1e-2 and v["theta"] < 6e-3, v
+    assert v["theta_bulk"] < 4e-3, v
 
 
 @pytest.mark.parametrize("thetas", THETAS)
@@ -109,6 +120,7 @@ def test_force_order_ranking(steady, thetas):
     variation, N = 2 closest; the sigma-bar terms change almost nothing."""
     e = {fo: steady[(*thetas, fo, False)]["theta"] for fo in (0, 1, 2)}
     assert e[0] > e[1] > e[2], e
+    assert e[1] > 4 * e[2] and e[0] > 4 * e[1], e  # measured: ~6-10x and ~5-7x
     with_sigma = steady[(*thetas, 2, True)]["prof"][2]
     d = np.max(np.abs(with_sigma - steady[(*thetas, 2, False)]["prof"][2]))
     assert d < 0.1 * e[2], (d, e[2])
