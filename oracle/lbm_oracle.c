@@ -23,29 +23,29 @@
  *     not from the expanded scalar form Eq. fi;
  *   - the update Eq. lbm with the mid-point state rho, u + g/2, theta.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open (numbered as in the design notes):
  *   R1  f in Eq. lbm is the auxiliary (pre-collision) distribution f~; the
  *       mid-point state is rho = sum f~, u = sum f~ xi / rho + g/2 and the
  *       physical temperature theta = (sum f~ xi^2/rho - |u~|^2)/D + g^2/(4D)
  *       with u~ = sum f~ xi / rho (this keeps the O(g^2) term so that the
  *       energy budget per step is exactly 2 rho g.u).
- *   R2  sigma-bar = -(1 - 1/(2 tau)) sum_i (f~_i - f0_i)(xi_i - u)(xi_i - u)
+ *   R2  tau passed in is the collision divisor tau-hat of Eq. lbm.
+ *   R8  sigma-bar = -(1 - 1/(2 tau)) sum_i (f~_i - f0_i)(xi_i - u)(xi_i - u)
  *       with u the mid-point velocity; it enters the force through
  *       a^(2) = a^(2)_0 - sigma (Eq. f2).  Off unless requested.
- *   R3  heat flux q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2)
+ *   R9  heat flux q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2)
  *       |xi_i - u|^2 (xi_i - u): the physical non-equilibrium part of the
  *       distribution (f0 carries no heat flux).
- *   R4  storage holds the post-collision distribution f*; a step pulls
- *       f~_i(x) = f*_i(x - e_i) and collides.  init places f~ = f0 - F/2 at
- *       the slots the first pull reads, so the pulled state at t = 0 is
- *       exactly the requested one (periodic and bounce-back walls).
- *   R5  walls (the paper's boundary rule is unpublished): half-way bounce-back
+ *   R10 walls (the paper's boundary rule is unpublished): half-way bounce-back
  *       keeping the column, f~_i(x) = f*_{-i}(x with x_a -> e_ia - 1 - x_a)
  *       at the low wall (mirrored at the high wall); the thermal wall fills
  *       the same slots with rho_w f0_i(1, 0, T_wall) where rho_w makes the
  *       column's incoming mass equal its outgoing mass.
- *   R6  tau passed in is the collision divisor tau-hat of Eq. lbm.
- *   R7  constant dynamic viscosity (the validation runs of Sec. 3 set
+ *   R11 storage holds the post-collision distribution f*; a step pulls
+ *       f~_i(x) = f*_i(x - e_i) and collides.  init places f~ = f0 - F/2 at
+ *       the slots the first pull reads, so the pulled state at t = 0 is
+ *       exactly the requested one (periodic and bounce-back walls).
+ *   R13 constant dynamic viscosity (the validation runs of Sec. 3 set
  *       tau = mu / (rho theta) so that mu and lambda stay uniform): with
  *       mu > 0 every site uses tau-hat = mu / (rho theta) + 1/2 with the
  *       mid-point rho and theta, in the update, sigma-bar and q.
@@ -280,7 +280,7 @@ typedef struct {
   int n[3];
   long N;
   double tau;
-  double mu;              /* > 0: constant dynamic viscosity (R7) */
+  double mu;              /* > 0: constant dynamic viscosity (R13) */
   int force_order, include_sigma;
   int bc[3];
   double Tw[3][2];        /* wall temperature, [axis][0 = low, 1 = high] */
@@ -424,7 +424,7 @@ static double pull(const orc_sim *S, const double *f, const int *x, int i) {
 }
 
 /* The slot of the post-collision state that the pull of (x, i) reads, for the
- * periodic and bounce-back maps (used to place the initial state, R4).     */
+ * periodic and bounce-back maps (used to place the initial state, R11).     */
 static long pull_source(const orc_sim *S, const int *x, int i) {
   int src[3];
   for (int a = 0; a < 3; ++a) {
@@ -472,7 +472,7 @@ static orc_state midpoint(const orc_lattice *L, const double *ft, const double *
   return m;
 }
 
-/* sigma-bar (R2). */
+/* sigma-bar (R8). */
 static void sigma_bar(const orc_lattice *L, double tau, const double *ft, const double *feq,
                       const double *u, double *sig) {
   int D = L->D;
@@ -486,7 +486,7 @@ static void sigma_bar(const orc_lattice *L, double tau, const double *ft, const 
   for (int k = 0; k < D * D; ++k) sig[k] *= -(1.0 - 0.5 / tau);
 }
 
-/* The collision divisor tau-hat at a site (R6 / R7). */
+/* The collision divisor tau-hat at a site (R2 / R13). */
 static double site_tau(const orc_sim *S, const orc_state *m) {
   return S->mu > 0.0 ? S->mu / (m->rho * m->theta) + 0.5 : S->tau;
 }
@@ -576,7 +576,7 @@ int orc_step_sites(void *h, const double *state, const long *sites, long nsites,
   return 0;
 }
 
-/* Physical mid-point moments rho, u (D*N), T (N), heat flux q (D*N, R3) and,
+/* Physical mid-point moments rho, u (D*N), T (N), heat flux q (D*N, R9) and,
  * optionally, sigma-bar (D*D*N) of the current state.  Any output may be NULL. */
 int orc_moments(void *h, double *rho, double *u, double *T, double *q, double *sigma) {
   orc_sim *S = (orc_sim *)h;
