@@ -126,7 +126,18 @@ typedef struct {
                         theta) so that mu and the conductivity stay uniform,
                         Sec. 3.1); the tau argument of lbm_create is then
                         unused.  0: constant tau-hat = tau (default)          */
+  int overlap_steps; /* 1: each plain step kernel is launched as a programmatic
+                        dependent of the previous kernel on the stream, so its
+                        blocks are scheduled while that kernel drains; they
+                        wait for its completion and memory (griddepcontrol.
+                        wait) before the first population load.  0: plain
+                        stream order.  -1 (default): on for grids of at least
+                        LBM_OVERLAP_MIN_SITES sites (on grids too small to
+                        fill the GPU its effect was within run-to-run noise).
+                        Results are identical either way.                    */
 } lbm_options;
+
+#define LBM_OVERLAP_MIN_SITES 131072
 
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2,
        LBM_KERNEL_PREFETCH = 3 /* persistent; each thread prefetches its next tile's
@@ -136,6 +147,10 @@ enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2,
 /* Fills *opt with the defaults: FP64, force_order 2, no sigma, fully periodic,
  * wall temperatures 1, NULL stream, library block shape, no graph. */
 void lbm_default_options(lbm_options *opt);
+
+/* sizeof(lbm_options) as compiled into the library, so that a binding can
+ * check its own copy of the struct layout before passing one in. */
+size_t lbm_options_size(void);
 
 /* Velocity set of a lattice: D, Q, c, the integer vectors e (Q*3, the
  * library's direction order: rest first, then opposite pairs), the weights w

@@ -43,7 +43,8 @@ class lbm_options(ctypes.Structure):
                 ("T_lo", ctypes.c_double * 3), ("T_hi", ctypes.c_double * 3),
                 ("stream", ctypes.c_void_p), ("block_x", ctypes.c_int),
                 ("graph_steps", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("tma_stages", ctypes.c_int), ("mu", ctypes.c_double)]
+                ("tma_stages", ctypes.c_int), ("mu", ctypes.c_double),
+                ("overlap_steps", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -65,6 +66,10 @@ def lib():
             raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
                                "(run paper_2302_04741_gb300.build.build())")
         L = ctypes.CDLL(LIB_PATH)
+        L.lbm_options_size.restype = ctypes.c_size_t
+        if L.lbm_options_size() != ctypes.sizeof(lbm_options):
+            raise RuntimeError(f"lbm_options layout mismatch: library {L.lbm_options_size()} B, "
+                               f"binding {ctypes.sizeof(lbm_options)} B")
         L.lbm_default_options.argtypes = [ctypes.POINTER(lbm_options)]
         L.lbm_default_options.restype = None
         L.lbm_lattice_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -311,7 +316,7 @@ def lbm_batch_destroy(b):
 # ------------------------------------------------------------ convenience
 def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
             T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0, kernel=LBM_KERNEL_AUTO,
-            tma_stages=0, mu=0.0, include_sigma=False):
+            tma_stages=0, mu=0.0, include_sigma=False, overlap_steps=-1):
     o = lbm_default_options()
     o.precision = precision
     o.force_order = force_order
@@ -326,6 +331,7 @@ def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0
     o.kernel = kernel
     o.tma_stages = tma_stages
     o.mu = mu
+    o.overlap_steps = int(overlap_steps)
     return o
 
 
@@ -337,7 +343,7 @@ class Sim:
     """
 
     def __init__(self, w, stream=None, block_x=0, graph_steps=0, precision=None,
-                 kernel=LBM_KERNEL_AUTO, tma_stages=0):
+                 kernel=LBM_KERNEL_AUTO, tma_stages=0, overlap_steps=-1):
         self.w = w
         self.lat = w["lattice"]
         self.D, self.Q, self.c, self.e, self.wts = lbm_lattice_info(self.lat)
@@ -347,7 +353,7 @@ class Sim:
         self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
                            w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
                            block_x, graph_steps, kernel, tma_stages, w.get("mu", 0.0),
-                           w.get("include_sigma", False))
+                           w.get("include_sigma", False), overlap_steps)
         g = w.get("g")
         self._gfield = g
         self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)

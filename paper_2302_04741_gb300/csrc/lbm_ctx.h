@@ -17,6 +17,7 @@ struct lbm_ctx {
   int N = 0;
   double tau = 0.0;
   lbm_options opt{};
+  bool overlap = false;        // step kernels launched as programmatic dependents
   int fo = 2;                  // kernel force-order code: opt.force_order, or 3 for
                                // order 2 with the sigma-bar terms
   const lbm::LatticeOps* ops = nullptr;

@@ -300,11 +300,16 @@ __global__ void __launch_bounds__(256, min_blocks<L, P>())
   const bool near = p.wall != W_NONE && (a < 3 || a >= nA - 3);
   const int wx0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   const bool interior = !near && wx0 >= 3 && wx0 + 31 <= p.nx - 4;
+  // Programmatic dependent launch: let the next step's blocks be scheduled
+  // now, and wait for the previous kernel (and its memory) before pulling.
+  // Both are no-ops when the launch has no programmatic dependency.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  R g[3];
+  site_force_r<L::D, R>(p, x, y, z, site, g);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   R d[L::Q];
   if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
   else pull<L, P, R>(fin, p, x, y, z, d);
-  R g[3];
-  site_force_r<L::D, R>(p, x, y, z, site, g);
   collide_store<L, P, FO>(d, g, site, fout, p);
 }
 

@@ -14,7 +14,7 @@ namespace lbm {
 struct LatticeOps {
   int Q, D;
   cudaError_t (*step)(int P, int FO, const void* fin, void* fout, const StepParams& p, int bx,
-                      cudaStream_t s);
+                      bool overlap, cudaStream_t s);
   cudaError_t (*init)(int P, int mode, const double* rho, const double* u, const double* T,
                       void* fout, unsigned* maxbits, int FO, const StepParams& p, cudaStream_t s);
   cudaError_t (*moments)(int P, const void* fin, double* rho, double* u, double* T, double* q,
@@ -47,12 +47,24 @@ struct Ops {
   template <int P>
   using T = typename Codec<P>::T;
 
+  // overlap: launch as a programmatic dependent of the stream's previous
+  // kernel (the step kernel waits with griddepcontrol.wait before its loads)
   static cudaError_t step(int P, int FO, const void* fin, void* fout, const StepParams& p, int bx,
-                          cudaStream_t s) {
-    const dim3 g = row_grid(p, bx), b(bx);
+                          bool overlap, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = row_grid(p, bx);
+    cfg.blockDim = dim3(bx);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = overlap ? 1 : 0;
+    cudaError_t e = cudaSuccess;
 #define LBM_STEP_CASE(PP, FF)                                                            \
   case PP * 4 + FF:                                                                      \
-    k_step<L, PP, FF><<<g, b, 0, s>>>((const T<PP>*)fin, (T<PP>*)fout, p);               \
+    e = cudaLaunchKernelEx(&cfg, k_step<L, PP, FF>, (const T<PP>*)fin, (T<PP>*)fout, p); \
     break;
     // FO 3: force order 2 with the sigma-bar terms (plain kernel only)
     switch (P * 4 + FO) {
@@ -62,7 +74,7 @@ struct Ops {
       default: return cudaErrorInvalidValue;
     }
 #undef LBM_STEP_CASE
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
 
   static cudaError_t init(int P, int mode, const double* rho, const double* u, const double* T_,

@@ -352,6 +352,19 @@ def test_translation_invariance_bitwise():
     np.testing.assert_array_equal(roll(a.get_state()), b.get_state())
 
 
+@pytest.mark.parametrize("graph_steps", [0, 10])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_overlapped_launches_are_bitwise_plain(precision, graph_steps):
+    """Programmatic dependent launch of successive steps changes nothing."""
+    w = workload(0, (200, 40, 1), seed=8, precision=precision, bc=(0, 2, 0),
+                 T_lo=(1.0, 1.05, 1.0), T_hi=(1.0, 0.95, 1.0))
+    a = lbm.Sim(w, overlap_steps=1, graph_steps=graph_steps).init()
+    b = lbm.Sim(w, overlap_steps=0, graph_steps=graph_steps).init()
+    a.step(30)
+    b.step(30)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+
+
 def test_errors_are_reported():
     w = workload(0, (16, 8, 1))
     s = lbm.Sim(w)
