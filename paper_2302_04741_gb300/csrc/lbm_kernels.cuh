@@ -395,47 +395,60 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
 }
 
 // ------------------------------------------------------------ moments
-// Physical rho, u, T and heat flux q in double (the FP64 diagnostic):
-// q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2) |xi_i - u|^2 (xi_i - u)
-// where f~_i - f0_i + F_i/2 = d_i - w_i [drho + rho (p_i - F'_i/2)].
-// With sigma-bar (FO 3) the odd force part gains (k / (2 rho)) [(g.xi)(xi.S.xi)
-// - 2 (S g).xi], k = 1 - om/2 (see stress_tensor).
-template <class L, int FO>
-__device__ __forceinline__ void heat_flux(const double (&d)[L::Q], const MidState<L, double>& m,
-                                          const double (&g)[3], double omega, double (&q)[3]) {
+// Physical rho, u, T and heat flux q in double (the FP64 diagnostic), with
+// q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2) |xi_i - u|^2 (xi_i - u).
+// Each of the three sums is a combination of moments of order <= 3, which
+// the quadrature integrates exactly for f0 and F (degree 9 >= 4 + 3 on
+// D2Q37, 7 >= 3 + 3 on D3Q39), so only the pulled f~ is summed per site:
+//   sum f0 |c|^2 c = 0 (the Maxwellian carries no heat flux), and with
+//   S = the second moment the force's n = 3 term contracts (rho (u u + theta
+//   delta), minus sigma-bar for FO 3; rho delta for orders 0 and 1) and
+//   M2 = sum F xi xi (rho (g u + u g) for orders >= 1, else 0),
+//   sum F |c|^2 c_a = 2 (S g)_a + g_a tr S - u_a tr M2 - 2 (M2 u)_a
+//                     + 2 rho u_a (u.g) + rho u^2 g_a,
+// which is (D + 2) rho theta g_a at order 2.  sum f~ |c|^2 c comes from the
+// raw moments of the deviations d = f~ - w: m0 = sum d, m1 = sum d e,
+// m2 = sum d e e, m3 = sum d |e|^2 e (c = xi - u, xi = c_lat e).
+template <class L>
+struct HeatMoments {
+  double m0, m1[3], m2[6], m3[3];  // m2 as (xx, yy, zz, xy, xz, yz)
+};
+
+template <class L>
+__device__ __forceinline__ HeatMoments<L> heat_moments(const double (&d)[L::Q]) {
   constexpr int NP = (L::Q - 1) / 2;
-  const double c = L::c;
-  q[0] = q[1] = q[2] = 0.0;
-  StressTerms<double> st;
-  if constexpr (FO == 3) {
-    double S[6];
-    stress_tensor<L, double>(d, m.drho, m.rho, m.theta_m1, m.u, g, S);
-    st = stress_terms<L, double>(S, g, 0.5 * (1.0 - 0.5 * omega) / m.rho);
-  }
-  auto add = [&](double fneq, double e0, double e1, double e2) {
-    const double c0 = c * e0 - m.u[0], c1 = c * e1 - m.u[1], c2 = c * e2 - m.u[2];
-    const double w = fneq * (c0 * c0 + c1 * c1 + c2 * c2);
-    q[0] = fma(w, c0, q[0]);
-    q[1] = fma(w, c1, q[1]);
-    q[2] = fma(w, c2, q[2]);
-  };
-  {
-    double E, Fe;
-    rest_terms<L, FO, double>(m, E, Fe);
-    add(d[0] - L::W(0) * fma(m.rho, E - 0.5 * Fe, m.drho), 0, 0, 0);
-  }
+  HeatMoments<L> h{};
+  h.m0 = d[0];
   static_for<0, NP>([&](auto K) {
     constexpr int ip = 2 * K + 1, im = ip + 1;
-    double E, O, Fe, Fo;
-    pair_terms<L, FO, ip, double>(m, E, O, Fe, Fo);
-    if constexpr (FO == 3) Fo += stress_pair<L, ip, double>(st);
-    constexpr double ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
-    add(d[ip] - L::W(ip) * fma(m.rho, (E + O) - 0.5 * (Fe + Fo), m.drho), ex, ey, ez);
-    add(d[im] - L::W(im) * fma(m.rho, (E - O) - 0.5 * (Fe - Fo), m.drho), -ex, -ey, -ez);
+    constexpr int ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
+    constexpr int e2 = ex * ex + ey * ey + ez * ez;
+    const double s = d[ip] + d[im];
+    const double a = d[ip] - d[im];
+    h.m0 += s;
+    h.m1[0] = mac<ex>(a, h.m1[0]);
+    h.m1[1] = mac<ey>(a, h.m1[1]);
+    h.m2[0] = mac<ex * ex>(s, h.m2[0]);
+    h.m2[1] = mac<ey * ey>(s, h.m2[1]);
+    h.m2[3] = mac<ex * ey>(s, h.m2[3]);
+    h.m3[0] = mac<e2 * ex>(a, h.m3[0]);
+    h.m3[1] = mac<e2 * ey>(a, h.m3[1]);
+    if constexpr (L::D == 3) {
+      h.m1[2] = mac<ez>(a, h.m1[2]);
+      h.m2[2] = mac<ez * ez>(s, h.m2[2]);
+      h.m2[4] = mac<ex * ez>(s, h.m2[4]);
+      h.m2[5] = mac<ey * ez>(s, h.m2[5]);
+      h.m3[2] = mac<e2 * ez>(a, h.m3[2]);
+    }
   });
-  const double k = 0.5 * (1.0 - 0.5 * omega);
-  q[0] *= k; q[1] *= k; q[2] *= k;
-  if (L::D == 2) q[2] = 0.0;
+  return h;
+}
+
+// Symmetric 3x3 (xx, yy, zz, xy, xz, yz) times a vector.
+__device__ __forceinline__ void sym_mul(const double (&S)[6], const double (&v)[3], double (&o)[3]) {
+  o[0] = S[0] * v[0] + S[3] * v[1] + S[4] * v[2];
+  o[1] = S[3] * v[0] + S[1] * v[1] + S[5] * v[2];
+  o[2] = S[4] * v[0] + S[5] * v[1] + S[2] * v[2];
 }
 
 template <class L, int P>
@@ -453,21 +466,67 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
   pull<L, P, double>(fin, p, x, y, z, d);
   double g[3];
   site_force<D>(p, x, y, z, site, g);
-  MidState<L, double> m;
-  midpoint_state<L, double>(d, g, m);
-  if (rho) rho[site] = m.rho;
-  if (T) T[site] = 1.0 + m.theta_m1;
-  if (u)
-    for (int a = 0; a < D; ++a) u[a * N + site] = m.u[a];
-  if (q) {
-    double qq[3];
-    const double om = site_omega<double>(p, m.rho, 1.0 + m.theta_m1);
-    if (force_order == 0) heat_flux<L, 0>(d, m, g, om, qq);
-    else if (force_order == 1) heat_flux<L, 1>(d, m, g, om, qq);
-    else if (force_order == 2) heat_flux<L, 2>(d, m, g, om, qq);
-    else heat_flux<L, 3>(d, m, g, om, qq);
-    for (int a = 0; a < D; ++a) q[a * N + site] = qq[a];
+  const HeatMoments<L> h = heat_moments<L>(d);
+  // mid-point state (R1), as in the step kernel
+  const double c = L::c, c2 = L::c2;
+  const double r = 1.0 + h.m0, ir = 1.0 / r;
+  double J[3], uu[3];
+  for (int a = 0; a < 3; ++a) {
+    J[a] = c * h.m1[a];  // sum f~ xi = rho u~
+    uu[a] = J[a] * ir + 0.5 * g[a];
   }
+  const double k2 = h.m2[0] + h.m2[1] + h.m2[2];
+  const double ut2 = (J[0] * J[0] + J[1] * J[1] + J[2] * J[2]) * ir * ir;
+  const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  const double Th = ((c2 * k2 - double(D) * h.m0) * ir - ut2) * (1.0 / D) + g2 * (0.25 / D);
+  if (rho) rho[site] = r;
+  if (T) T[site] = 1.0 + Th;
+  if (u)
+    for (int a = 0; a < D; ++a) u[a * N + site] = uu[a];
+  if (!q) return;
+  const double om = site_omega<double>(p, r, 1.0 + Th);
+  const double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+  const double ug = uu[0] * g[0] + uu[1] * g[1] + uu[2] * g[2];
+  const double uJ = uu[0] * J[0] + uu[1] * J[1] + uu[2] * J[2];
+  // sum f~ |c|^2 c with P = c^2 m2 (so sum f~ xi xi = delta + P)
+  double Pm[6], Pu[3];
+  for (int k = 0; k < 6; ++k) Pm[k] = c2 * h.m2[k];
+  sym_mul(Pm, uu, Pu);
+  const double c3 = c * c2;
+  double C3[3];
+  for (int a = 0; a < 3; ++a)
+    C3[a] = c3 * h.m3[a] - double(D + 2) * uu[a] - uu[a] * (c2 * k2) - 2.0 * Pu[a] +
+            2.0 * uu[a] * uJ + u2 * J[a] - u2 * uu[a] * r;
+  // sum F |c|^2 c
+  double FC3[3];
+  const double th = 1.0 + Th;
+  if (force_order >= 2) {
+    for (int a = 0; a < 3; ++a) FC3[a] = double(D + 2) * r * th * g[a];
+    if (force_order == 3) {
+      // S = rho (u u + theta delta) - sigma-bar, sigma-bar = -(1 - om/2) S_st
+      double Sst[6], Sg[3];
+      const double iso = fma(r, Th, h.m0);
+      const double hr = 0.5 * r;
+      auto conv = [&](int a, int b) { return hr * (uu[a] * (g[b] - uu[b]) + uu[b] * (g[a] - uu[a])); };
+      Sst[0] = Pm[0] - iso + conv(0, 0);
+      Sst[1] = Pm[1] - iso + conv(1, 1);
+      Sst[2] = D == 3 ? Pm[2] - iso + conv(2, 2) : 0.0;
+      Sst[3] = Pm[3] + conv(0, 1);
+      Sst[4] = D == 3 ? Pm[4] + conv(0, 2) : 0.0;
+      Sst[5] = D == 3 ? Pm[5] + conv(1, 2) : 0.0;
+      sym_mul(Sst, g, Sg);
+      const double kf = 1.0 - 0.5 * om;
+      for (int a = 0; a < 3; ++a) FC3[a] += 2.0 * kf * Sg[a];
+    }
+  } else {
+    // S = rho delta; M2 = rho (g u + u g) at order 1, 0 at order 0
+    for (int a = 0; a < 3; ++a) {
+      FC3[a] = double(D + 2) * r * g[a] + 2.0 * r * uu[a] * ug + r * u2 * g[a];
+      if (force_order == 1) FC3[a] -= 2.0 * r * uu[a] * ug + 2.0 * r * (g[a] * u2 + uu[a] * ug);
+    }
+  }
+  const double kq = 0.5 * (1.0 - 0.5 * om);
+  for (int a = 0; a < D; ++a) q[a * N + site] = kq * (C3[a] + 0.5 * FC3[a]);
 }
 
 // ------------------------------------------------- conservation sums (FP64)
