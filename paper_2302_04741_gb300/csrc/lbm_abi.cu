@@ -108,6 +108,22 @@ bool is_device_ptr(const void* ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// A pointer kernels can dereference for `ptr`: device and managed memory as
+// is, page-locked host memory through its mapped device address (kernels then
+// read or write host memory directly over the host link, overlapped with their
+// arithmetic, instead of a staging copy); nullptr for pageable host memory.
+template <class T>
+T* device_view(T* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return ptr;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<T*>(a.devicePointer);
+  return nullptr;
+}
+
 int ensure_tmp(lbm_ctx* c) {
   if (c->tmp) return LBM_OK;
   const size_t n = (size_t)(2 + 2 * c->D) * c->N;
@@ -508,8 +524,8 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
   if (!rho || !u || !T) return fail(c, LBM_EINVAL, "rho, u and T are required");
   LBM_CUDA(c, cudaSetDevice(c->device));
   const size_t N = (size_t)c->N;
-  const double *drho = rho, *du = u, *dT = T;
-  const bool dev = is_device_ptr(rho) && is_device_ptr(u) && is_device_ptr(T);
+  const double *drho = device_view(rho), *du = device_view(u), *dT = device_view(T);
+  const bool dev = drho && du && dT;
   if (!dev) {
     int rc = ensure_tmp(c);
     if (rc) return rc;
@@ -519,7 +535,6 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
     LBM_CUDA(c, cudaMemcpyAsync(t + (1 + c->D) * N, T, N * sizeof(double), cudaMemcpyDefault, c->stream));
     drho = t; du = t + N; dT = t + (1 + c->D) * N;
   }
-  drop_graphs(c);
   c->cur = 0;
   if (c->opt.precision == LBM_FP16_SCALED) {
     LBM_CUDA(c, cudaMemsetAsync(c->dmax, 0, sizeof(unsigned), c->stream));
@@ -536,11 +551,15 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
     if (mx > 0.f) k = 12 - (int)std::floor(std::log2((double)mx));
     if (k > 60) k = 60;
     if (k < -60) k = -60;
-    c->p.h_scale = std::ldexp(1.0f, k);
+    const float scale = std::ldexp(1.0f, k);
+    if (scale != c->p.h_scale) drop_graphs(c);  // captured launches hold the old scale
+    c->p.h_scale = scale;
     c->p.h_inv_scale = std::ldexp(1.0f, -k);
   }
   LBM_CUDA(c, c->ops->init(c->opt.precision, 1, drho, du, dT, c->f[0], nullptr, c->opt.force_order, c->p, c->stream));
-  if (!dev) LBM_CUDA(c, cudaStreamSynchronize(c->stream));  // host arrays may be freed after return
+  // host arrays (staged or read in place) may be freed after return
+  if (!is_device_ptr(rho) || !is_device_ptr(u) || !is_device_ptr(T))
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   c->initialised = true;
   c->steps = 0;
   lbm::batch_mark_dirty(c->batch);  // buffer parity and FP16 scale may have changed
@@ -581,16 +600,18 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* T, double* q) {
   double* outs[4] = {rho, u, T, q};
   const size_t cnt[4] = {N, c->D * N, N, c->D * N};
   double* dst[4];
+  bool staged[4];
   double* t = c->tmp;
   for (int k = 0; k < 4; ++k) {
-    dst[k] = nullptr;
-    if (outs[k]) dst[k] = is_device_ptr(outs[k]) ? outs[k] : t;
+    dst[k] = outs[k] ? device_view(outs[k]) : nullptr;
+    staged[k] = outs[k] && !dst[k];
+    if (staged[k]) dst[k] = t;
     t += cnt[k];
   }
   LBM_CUDA(c, c->ops->moments(c->opt.precision, c->f[c->cur], dst[0], dst[1], dst[2], dst[3],
                               c->fo, c->p, c->stream));
   for (int k = 0; k < 4; ++k)
-    if (outs[k] && dst[k] != outs[k])
+    if (staged[k])
       LBM_CUDA(c, cudaMemcpyAsync(outs[k], dst[k], cnt[k] * sizeof(double), cudaMemcpyDefault, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
