@@ -175,6 +175,22 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
  * grid's scale.  Resets the step counter. */
 int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *T);
 
+/* Marks solid sites: walls of any shape as a staircase of sites (the
+ * curved walls of the paper's concentric-cylinder test, Sec. 3.2; the paper
+ * leaves the wall rule unpublished, so this is the library's own).  solid: N
+ * bytes, non-zero = solid; T_wall: N doubles, the wall temperature of each
+ * solid site (> 0; ignored at fluid sites); host memory, copied.  A fluid
+ * site x whose pull source y = x - e_i is solid receives the diffuse-wall
+ * population rho_w(x) f0_i(1, 0, T_y); rho_w(x) makes the mass the walls emit
+ * into x equal the mass x sends into solid sites in the same step, so every
+ * fluid site keeps its mass.  Solid sites are not stepped and report zeros
+ * from lbm_moments and lbm_get_populations; lbm_conserved sums fluid sites.
+ * Requires all axes periodic, FP64 or FP32-shifted storage and the plain
+ * step kernel (batches reject such contexts), and must precede lbm_init
+ * (LBM_ESTATE after it).  Not stored by lbm_save: set it again before
+ * lbm_load. */
+int lbm_set_solid(lbm_ctx *ctx, const unsigned char *solid, const double *T_wall);
+
 /* Advances n >= 0 steps (one fused pull-stream + collide launch per step, or
  * graph replays).  Asynchronous on the context's stream. */
 int lbm_step(lbm_ctx *ctx, int n);

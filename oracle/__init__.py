@@ -71,6 +71,7 @@ def _load():
                                             ctypes.c_double, _dp]
             lib.orc_force.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp,
                                       ctypes.c_double, _dp, _dp, _dp]
+            lib.orc_set_solid.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_ubyte), _dp]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_get_threads.restype = ctypes.c_int
             _lib = lib
@@ -173,6 +174,16 @@ class OracleSim:
         if getattr(self, "h", None):
             self.lib.orc_destroy(self.h)
             self.h = None
+
+    def set_solid(self, solid, T_wall):
+        """Solid sites (N flags) with wall temperatures (N) -- curved walls as a
+        staircase of diffuse thermal walls; fully periodic grids only, before
+        init."""
+        solid = np.ascontiguousarray(np.asarray(solid).reshape(self.N) != 0, dtype=np.uint8)
+        T_wall = _f64(np.asarray(T_wall).reshape(self.N))
+        if self.lib.orc_set_solid(self.h, solid.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                  _p(T_wall)):
+            raise ValueError("orc_set_solid rejected the arguments")
 
     def init(self, rho, u, T):
         rho = _f64(np.asarray(rho).reshape(self.N))

@@ -49,6 +49,11 @@
  *       tau = mu / (rho theta) so that mu and lambda stay uniform): with
  *       mu > 0 every site uses tau-hat = mu / (rho theta) + 1/2 with the
  *       mid-point rho and theta, in the update, sigma-bar and q.
+ *   R15 solid sites (curved walls, staircase): a slot of a fluid site x
+ *       pulled from a solid site y = x - e_i holds rho_w(x) f0_i(1, 0, T_y);
+ *       rho_w(x) makes the mass x emits into solid sites (its post-collision
+ *       slots -e_i) equal the mass the walls emit into x.  Links are not
+ *       traced: only the source site decides.
  */
 #include <math.h>
 #include <stdio.h>
@@ -291,6 +296,9 @@ typedef struct {
   double *fn;             /* Q * N scratch for the next state */
   double *rho_w;          /* 2 * (N / n_wall) wall densities of the current step */
   int wall_axis;          /* -1 if fully periodic */
+  unsigned char *solid;   /* N flags (R15), NULL without solid sites */
+  double *E_solid;        /* Q * N: f0_i(1, 0, T_wall) at solid sites */
+  double *rho_ws;         /* N wall densities of the fluid sites of the current step */
 } orc_sim;
 
 static long site_index(const orc_sim *S, const int *x) {
@@ -320,6 +328,7 @@ void orc_destroy(void *h) {
   orc_sim *S = (orc_sim *)h;
   if (!S) return;
   free(S->g); free(S->f); free(S->fn); free(S->rho_w);
+  free(S->solid); free(S->E_solid); free(S->rho_ws);
   free(S);
 }
 
@@ -374,10 +383,57 @@ void *orc_create(int lat, int nx, int ny, int nz, double tau, double mu, int for
   return S;
 }
 
+static long neighbour(const orc_sim *S, const int *x, const int *e, int sign) {
+  int y[3];
+  for (int a = 0; a < 3; ++a) y[a] = wrap(x[a] + sign * e[a], S->n[a]);
+  return site_index(S, y);
+}
+
+/* Solid sites (R15, fully periodic grids only): solid[s] != 0 marks a wall
+ * site at temperature T[s].  Must precede orc_init.                        */
+int orc_set_solid(void *h, const unsigned char *solid, const double *T) {
+  orc_sim *S = (orc_sim *)h;
+  if (S->wall_axis >= 0 || !solid || !T) return -1;
+  const int Q = S->L.Q;
+  S->solid = (unsigned char *)malloc((size_t)S->N);
+  S->E_solid = (double *)calloc((size_t)Q * S->N, sizeof(double));
+  S->rho_ws = (double *)calloc((size_t)S->N, sizeof(double));
+  if (!S->solid || !S->E_solid || !S->rho_ws) return -1;
+  double zero[3] = {0, 0, 0};
+  for (long k = 0; k < S->N; ++k) {
+    S->solid[k] = solid[k] ? 1 : 0;
+    if (S->solid[k]) equilibrium(&S->L, S->L.neq, 1.0, zero, T[k], S->E_solid + (size_t)k * Q);
+  }
+  return 0;
+}
+
+/* Wall densities of the solid sites' diffuse walls (R15): at a fluid site x,
+ * rho_w(x) = (mass of the slots of x about to move into solid sites) / (mass
+ * of f0(1, 0, T_wall) over the slots of x pulled from solid sites).       */
+static void solid_densities(orc_sim *S, const double *f) {
+  const int Q = S->L.Q;
+#pragma omp parallel for schedule(static)
+  for (long s = 0; s < S->N; ++s) {
+    S->rho_ws[s] = 0.0;
+    if (S->solid[s]) continue;
+    int x[3];
+    site_coords(S, s, x);
+    double out = 0.0, in = 0.0;
+    for (int i = 0; i < Q; ++i) {
+      long src = neighbour(S, x, S->L.e[i], -1);
+      if (!S->solid[src]) continue;
+      out += f[(long)S->L.opp[i] * S->N + s];
+      in += S->E_solid[(size_t)src * Q + i];
+    }
+    if (in > 0.0) S->rho_ws[s] = out / in;
+  }
+}
+
 /* Wall densities of the thermal (diffuse) wall for the state f: per column and
  * side, rho_w = (mass of the slots about to leave through that wall) / (mass
  * of f0(1, 0, T_wall) over the slots the wall fills).                      */
 static void wall_densities(orc_sim *S, const double *f) {
+  if (S->solid) solid_densities(S, f);
   int a = S->wall_axis;
   if (a < 0 || S->bc[a] != ORC_THERMAL_WALL) return;
   long ncol = S->N / S->n[a];
@@ -413,7 +469,11 @@ static double pull(const orc_sim *S, const double *f, const int *x, int i) {
       }
     }
   }
-  if (wa < 0) return f[i * S->N + site_index(S, src)];
+  if (wa < 0) {
+    long k = site_index(S, src);
+    if (S->solid && S->solid[k]) return S->rho_ws[site_index(S, x)] * S->E_solid[(size_t)k * S->L.Q + i];
+    return f[i * S->N + k];
+  }
   if (S->bc[wa] == ORC_BOUNCE_BACK) {
     int m[3] = {x[0], x[1], x[2]};
     m[wa] = side == 0 ? S->L.e[i][wa] - 1 - x[wa] : 2 * S->n[wa] - 1 - (x[wa] - S->L.e[i][wa]);
@@ -522,6 +582,7 @@ int orc_init(void *h, const double *rho, const double *u, const double *T) {
   int D = L->D;
 #pragma omp parallel for schedule(static)
   for (long s = 0; s < S->N; ++s) {
+    if (S->solid && S->solid[s]) continue;
     int x[3];
     double uu[3] = {0, 0, 0}, gg[3] = {0, 0, 0}, feq[ORC_QMAX], F[ORC_QMAX];
     site_coords(S, s, x);
@@ -531,7 +592,15 @@ int orc_init(void *h, const double *rho, const double *u, const double *T) {
     }
     equilibrium(L, L->neq, rho[s], uu, T[s], feq);
     force(L, S->force_order, rho[s], uu, T[s], gg, NULL, F);
-    for (int i = 0; i < L->Q; ++i) S->f[pull_source(S, x, i)] = feq[i] - 0.5 * F[i];
+    for (int i = 0; i < L->Q; ++i) {
+      if (S->solid && S->solid[neighbour(S, x, L->e[i], -1)]) {
+        /* pulled from a solid site: the wall emits it; the slot the wall
+         * absorbs (the opposite direction, at x) holds the local value */
+        S->f[(long)L->opp[i] * S->N + s] = feq[L->opp[i]] - 0.5 * F[L->opp[i]];
+        continue;
+      }
+      S->f[pull_source(S, x, i)] = feq[i] - 0.5 * F[i];
+    }
   }
   return 0;
 }
@@ -550,6 +619,7 @@ int orc_step(void *h, int nsteps) {
 #pragma omp parallel for schedule(static)
     for (long s = 0; s < S->N; ++s) {
       double ft[ORC_QMAX], out[ORC_QMAX], g[3];
+      if (S->solid && S->solid[s]) continue;
       gather(S, S->f, s, ft, g);
       collide(S, ft, g, out, NULL, NULL, NULL, NULL);
       for (int i = 0; i < S->L.Q; ++i) S->fn[i * S->N + s] = out[i];
@@ -587,6 +657,17 @@ int orc_moments(void *h, double *rho, double *u, double *T, double *q, double *s
   for (long s = 0; s < S->N; ++s) {
     double ft[ORC_QMAX], g[3], feq[ORC_QMAX], F[ORC_QMAX], sig[9];
     orc_state m;
+    if (S->solid && S->solid[s]) {  /* solid sites report zeros */
+      if (rho) rho[s] = 0.0;
+      if (T) T[s] = 0.0;
+      for (int a = 0; a < D; ++a) {
+        if (u) u[a * S->N + s] = 0.0;
+        if (q) q[a * S->N + s] = 0.0;
+      }
+      if (sigma)
+        for (int k = 0; k < D * D; ++k) sigma[(long)k * S->N + s] = 0.0;
+      continue;
+    }
     gather(S, S->f, s, ft, g);
     collide(S, ft, g, NULL, &m, feq, F, sig);
     if (rho) rho[s] = m.rho;
@@ -634,7 +715,8 @@ int orc_pull_state(void *h, double *ft) {
   for (long s = 0; s < S->N; ++s) {
     int x[3];
     site_coords(S, s, x);
-    for (int i = 0; i < S->L.Q; ++i) ft[i * S->N + s] = pull(S, S->f, x, i);
+    const int solid = S->solid && S->solid[s];
+    for (int i = 0; i < S->L.Q; ++i) ft[i * S->N + s] = solid ? 0.0 : pull(S, S->f, x, i);
   }
   return 0;
 }

@@ -81,6 +81,7 @@ def lib():
         for name in ("lbm_init",):
             getattr(L, name).argtypes = [_vp, _vp, _vp, _vp]
         L.lbm_step.argtypes = [_vp, ctypes.c_int]
+        L.lbm_set_solid.argtypes = [_vp, ctypes.POINTER(ctypes.c_ubyte), _dp]
         L.lbm_moments.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.lbm_conserved.argtypes = [_vp, _dp, _dp, _dp]
         for name in ("lbm_get_populations", "lbm_get_state", "lbm_set_state"):
@@ -186,6 +187,14 @@ def lbm_init(ctx, rho, u, T):
 
 def lbm_step(ctx, n):
     _check(lib().lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_set_solid(ctx, solid, T_wall):
+    """solid: N flags (non-zero = solid); T_wall: N wall temperatures (host)."""
+    s = np.ascontiguousarray(np.asarray(solid).ravel() != 0, dtype=np.uint8)
+    t = np.ascontiguousarray(np.asarray(T_wall, dtype=np.float64).ravel())
+    _check(lib().lbm_set_solid(ctx, s.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                               t.ctypes.data_as(_dp)), ctx)
 
 
 def lbm_moments(ctx, rho=None, u=None, T=None, q=None):
@@ -367,6 +376,9 @@ class Sim:
             self.ctx = None
 
     def init(self, rho=None, u=None, T=None):
+        if self.w.get("solid") is not None and not getattr(self, "_solid_set", False):
+            lbm_set_solid(self.ctx, self.w["solid"], self.w["T_wall"])
+            self._solid_set = True
         rho = self.w["rho"] if rho is None else rho
         u = self.w["u"] if u is None else u
         T = self.w["T"] if T is None else T

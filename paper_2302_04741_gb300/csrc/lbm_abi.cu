@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_launch.cuh"
@@ -566,6 +567,47 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
   return LBM_OK;
 }
 
+int lbm_set_solid(lbm_ctx* c, const unsigned char* solid, const double* T_wall) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!solid || !T_wall) return fail(c, LBM_EINVAL, "solid and T_wall are required");
+  if (c->initialised) return fail(c, LBM_ESTATE, "lbm_set_solid must precede lbm_init");
+  if (c->batch) return fail(c, LBM_ESTATE, "ctx is in a batch");
+  if (c->p.wall != lbm::W_NONE) return fail(c, LBM_EINVAL, "solid sites need all axes periodic");
+  if (c->opt.precision == LBM_FP16_SCALED)
+    return fail(c, LBM_EINVAL, "solid sites run with FP64 or FP32-shifted storage");
+  if (c->use_tma || c->use_async) return fail(c, LBM_EINVAL, "solid sites run in the plain step kernel");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const size_t N = (size_t)c->N;
+  std::vector<unsigned char> s(N);
+  std::vector<double> th(N, 0.0);
+  std::vector<float> thf(N, 0.f);
+  for (size_t k = 0; k < N; ++k) {
+    s[k] = solid[k] ? 1 : 0;
+    if (s[k]) {
+      if (!(T_wall[k] > 0.0) || !std::isfinite(T_wall[k]))
+        return fail(c, LBM_EINVAL, "wall temperature at site %zu must be positive", k);
+      th[k] = T_wall[k] - 1.0;
+      thf[k] = (float)th[k];
+    }
+  }
+  if (!c->solid) {
+    if (cudaMalloc(&c->solid, N) != cudaSuccess || cudaMalloc(&c->wall_th, N * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->wall_th_f, N * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, LBM_ENOMEM, "device allocation of the solid-site tables failed");
+    }
+    c->bytes += N * (1 + sizeof(double) + sizeof(float));
+  }
+  LBM_CUDA(c, cudaMemcpy(c->solid, s.data(), N, cudaMemcpyHostToDevice));
+  LBM_CUDA(c, cudaMemcpy(c->wall_th, th.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  LBM_CUDA(c, cudaMemcpy(c->wall_th_f, thf.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+  c->p.solid = c->solid;
+  c->p.wall_th = c->wall_th;
+  c->p.wall_th_f = c->wall_th_f;
+  drop_graphs(c);
+  return LBM_OK;
+}
+
 int lbm_step(lbm_ctx* c, int n) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
   if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0 (got %d)", n);
@@ -799,6 +841,9 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->f[1]);
   cudaFree(c->gtab);
   cudaFree(c->gtab_f);
+  cudaFree(c->solid);
+  cudaFree(c->wall_th);
+  cudaFree(c->wall_th_f);
   cudaFree(c->part);
   cudaFree(c->bad);
   cudaFree(c->dres);

@@ -201,6 +201,7 @@ int lbm_batch_add(lbm_batch* b, lbm_ctx* c) {
   if (!c->initialised) return bfail(b, LBM_ESTATE, "ctx is not initialised");
   if (c->lat != b->lat || c->opt.precision != b->precision || c->fo != b->force_order)
     return bfail(b, LBM_EINVAL, "ctx lattice / precision / force order differ from the batch");
+  if (c->solid) return bfail(b, LBM_EINVAL, "ctx has solid sites (plain step kernel only)");
   if (c->stream != b->stream) return bfail(b, LBM_EINVAL, "ctx must use the batch's stream");
   if (c->device != b->device) return bfail(b, LBM_EINVAL, "ctx lives on another device");
   if ((int)b->members.size() >= b->cap) return bfail(b, LBM_ENOMEM, "batch is full (%d)", b->cap);

@@ -26,6 +26,9 @@ struct lbm_ctx {
   int cur = 0;                 // f[cur] holds the current post-collision state
   double* gtab = nullptr;      // force table / field
   float* gtab_f = nullptr;     // its float copy (float kernels)
+  unsigned char* solid = nullptr;  // solid-site flags (lbm_set_solid), N bytes
+  double* wall_th = nullptr;   // wall temperature - 1 per site, N doubles
+  float* wall_th_f = nullptr;  // its float copy
   double* part = nullptr;      // conservation partials (2 * NCONS per block)
   unsigned* bad = nullptr;     // bad-site counts per block
   double* dres = nullptr;      // final reduction result

@@ -48,6 +48,12 @@ struct StepParams {
   float mu_f;
   float g0_f[3];
   const float* gtab_f;  // float copy of gtab (same layout)
+  // solid sites (staircase walls, fully periodic grids): flag per site and
+  // wall temperature minus 1 per site (read at solid sites only); nullptr
+  // when the grid has none
+  const unsigned char* solid;
+  const double* wall_th;
+  const float* wall_th_f;
 };
 
 // The parameters a kernel of arithmetic type R reads.
@@ -55,6 +61,7 @@ template <class R>
 struct ParamsOf;
 template <>
 struct ParamsOf<double> {
+  __device__ __forceinline__ static double wall_th(const StepParams& p, int k) { return __ldg(p.wall_th + k); }
   __device__ __forceinline__ static double omega(const StepParams& p) { return p.omega; }
   __device__ __forceinline__ static double mu(const StepParams& p) { return p.mu; }
   __device__ __forceinline__ static double g0(const StepParams& p, int a) { return p.g0[a]; }
@@ -62,6 +69,7 @@ struct ParamsOf<double> {
 };
 template <>
 struct ParamsOf<float> {
+  __device__ __forceinline__ static float wall_th(const StepParams& p, int k) { return __ldg(p.wall_th_f + k); }
   __device__ __forceinline__ static float omega(const StepParams& p) { return p.omega_f; }
   __device__ __forceinline__ static float mu(const StepParams& p) { return p.mu_f; }
   __device__ __forceinline__ static float g0(const StepParams& p, int a) { return p.g0_f[a]; }

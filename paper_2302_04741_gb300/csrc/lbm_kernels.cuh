@@ -129,6 +129,70 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
   });
 }
 
+// ------------------------------------------------------- solid sites
+// A solid site y emits into a fluid neighbour x = y + e_i the wall
+// Maxwellian rho_w(x) f0_i(1, 0, T_y) (diffuse thermal wall on a staircase):
+// f0_i(1, 0, T) / w_i = 1 + A0 with, for |xi_i|^2 = X2 and Th = T - 1,
+//   A0 = Th (X2 - D) / 2 + [NEQ 4] Th^2 (X2^2 - 2 (D + 2) X2 + D (D + 2)) / 8.
+// rho_w(x) equals the mass x sends into solid sites (its post-collision slots
+// -e_i of the solid-sourced directions) over sum_i f0_i(1, 0, T_y), so every
+// fluid site keeps its mass.  In deviations:
+//   rho_w - 1 = sum (d*_-i - w_i A0_i) / sum w_i (1 + A0_i),
+//   d_i = w_i ((rho_w - 1)(1 + A0_i) + A0_i).
+template <class L, int I, class R>
+__device__ __forceinline__ R wall_a0(R th) {
+  constexpr int D = L::D;
+  constexpr double X2 = L::c2 * double(L::E2(L::SH(I)));
+  R a0 = R(0.5 * (X2 - D)) * th;
+  if constexpr (L::NEQ >= 4) {
+    constexpr double q2 = (X2 * X2 - 2.0 * (D + 2) * X2 + double(D * (D + 2))) / 8.0;
+    a0 = fma(R(q2) * th, th, a0);
+  }
+  return a0;
+}
+
+// Pull of a fluid site of a grid with solid sites (all axes periodic).
+template <class L, int P, class RR>
+__device__ __forceinline__ void pull_solid(const typename Codec<P>::T* __restrict__ fin,
+                                           const StepParams& p, int x, int y, int z, int site,
+                                           RR (&d)[L::Q]) {
+  using C = Codec<P>;
+  constexpr int D = L::D, Q = L::Q;
+  const int nx = p.nx, ny = p.ny, nz = p.nz;
+  const size_t N = (size_t)p.N;
+  int xs[7], ys[7], zs[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    xs[k] = wrap3(x - (k - 3), nx);
+    ys[k] = wrap3(y - (k - 3), ny) * nx;
+    zs[k] = D == 3 ? wrap3(z - (k - 3), nz) * nx * ny : 0;
+  }
+  RR num = RR(0), den = RR(0);
+  unsigned long long walls = 0;
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
+    const int src = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
+    if (__ldg(p.solid + src)) {
+      constexpr int io = opposite<i>();
+      constexpr RR w = RR(L::W(i));
+      const RR a0 = wall_a0<L, i, RR>(ParamsOf<RR>::wall_th(p, src));
+      num += RR(C::template decode<L, io>(C::load(fin + io * N + site), p)) - w * a0;
+      den = fma(w, RR(1) + a0, den);
+      walls |= 1ull << i;
+      d[i] = a0;  // kept for the second pass
+    } else {
+      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + src), p));
+    }
+  });
+  if (!walls) return;
+  const RR rm1 = num / den;
+  static_for<0, Q>([&](auto I) {
+    constexpr int i = I;
+    if (walls >> i & 1ull) d[i] = RR(L::W(i)) * fma(rm1, RR(1) + d[i], d[i]);
+  });
+}
+
 // Pull for a warp whose 32 sites neither wrap around x nor touch a wall: every
 // source offset relative to the thread's own site, i*N + (row / plane shift)
 // - e_ix, is the same for the whole block (rows wrap only through the block's
@@ -286,7 +350,9 @@ constexpr int min_blocks() {
   return P == P_FP64 ? 1 : (L::Q > 37 ? 2 : LBM_FLOAT_D2Q37_BLOCKS);
 }
 
-template <class L, int P, int FO>
+// SOLID: the grid has solid sites (they are skipped; their fluid neighbours
+// take the diffuse-wall pull).
+template <class L, int P, int FO, bool SOLID = false>
 __global__ void __launch_bounds__(256, min_blocks<L, P>())
     k_step(const typename Codec<P>::T* __restrict__ fin, typename Codec<P>::T* __restrict__ fout,
            const StepParams p) {
@@ -295,6 +361,17 @@ __global__ void __launch_bounds__(256, min_blocks<L, P>())
   if (x >= p.nx) return;
   const int y = blockIdx.y, z = blockIdx.z;
   const int site = (z * p.ny + y) * p.nx + x;
+  if constexpr (SOLID) {
+    if (__ldg(p.solid + site)) return;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    R g[3];
+    site_force_r<L::D, R>(p, x, y, z, site, g);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    R d[L::Q];
+    pull_solid<L, P, R>(fin, p, x, y, z, site, d);
+    collide_store<L, P, FO>(d, g, site, fout, p);
+    return;
+  }
   const int a = L::D == 2 ? y : z;
   const int nA = L::D == 2 ? p.ny : p.nz;
   const bool near = p.wall != W_NONE && (a < 3 || a >= nA - 3);
@@ -353,6 +430,7 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int site = (z * ny + y) * nx + x;
   const size_t N = (size_t)p.N;
+  if (p.solid && p.solid[site]) return;
   double gd[3];
   site_force<D>(p, x, y, z, site, gd);
   const R g[3] = {R(gd[0]), R(gd[1]), R(gd[2])};
@@ -389,7 +467,15 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
       const int sx = wrap3(x - ex, nx);
       const int sy = wrap3(y - ey, ny);
       const int sz = D == 3 ? wrap3(z - ez, nz) : 0;
-      fout[i * N + (sz * ny + sy) * nx + sx] = C::template encode<L, i>(d[i], p);
+      const int src = (sz * ny + sy) * nx + sx;
+      if (p.solid && p.solid[src]) {
+        // pulled from a solid site: the wall emits it; the slot the wall
+        // absorbs (-e_i, at this site) holds the local value
+        constexpr int io = opposite<i>();
+        fout[io * N + site] = C::template encode<L, io>(d[io], p);
+      } else {
+        fout[i * N + src] = C::template encode<L, i>(d[i], p);
+      }
     }
   });
 }
@@ -462,8 +548,18 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
   const int y = blockIdx.y, z = blockIdx.z;
   const int site = (z * p.ny + y) * p.nx + x;
   const size_t N = (size_t)p.N;
+  if (p.solid && p.solid[site]) {  // solid sites report zeros
+    if (rho) rho[site] = 0.0;
+    if (T) T[site] = 0.0;
+    for (int a = 0; a < D; ++a) {
+      if (u) u[a * N + site] = 0.0;
+      if (q) q[a * N + site] = 0.0;
+    }
+    return;
+  }
   double d[Q];
-  pull<L, P, double>(fin, p, x, y, z, d);
+  if (p.solid) pull_solid<L, P, double>(fin, p, x, y, z, site, d);
+  else pull<L, P, double>(fin, p, x, y, z, d);
   double g[3];
   site_force<D>(p, x, y, z, site, g);
   const HeatMoments<L> h = heat_moments<L>(d);
@@ -614,8 +710,10 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
     const int x = xt * 128 + threadIdx.x;
     if (x >= p.nx) continue;
     const int site = (z * p.ny + y) * p.nx + x;
+    if (p.solid && p.solid[site]) continue;
     R d[Q];
-    pull<L, P, R>(fin, p, x, y, z, d);
+    if (p.solid) pull_solid<L, P, R>(fin, p, x, y, z, site, d);
+    else pull<L, P, R>(fin, p, x, y, z, d);
     double g[3];
     site_force<D>(p, x, y, z, site, g);
     const RawMoments<L, R> r = raw_moments<L, R>(d);
@@ -659,8 +757,13 @@ __global__ void __launch_bounds__(128) k_get_pulled(const typename Codec<P>::T* 
   const int y = blockIdx.y, z = blockIdx.z;
   const int site = (z * p.ny + y) * p.nx + x;
   const size_t N = (size_t)p.N;
+  if (p.solid && p.solid[site]) {
+    static_for<0, Q>([&](auto I) { out[int(I) * N + site] = 0.0; });
+    return;
+  }
   double d[Q];
-  pull<L, P, double>(fin, p, x, y, z, d);
+  if (p.solid) pull_solid<L, P, double>(fin, p, x, y, z, site, d);
+  else pull<L, P, double>(fin, p, x, y, z, d);
   static_for<0, Q>([&](auto I) {
     constexpr int i = I;
     out[i * N + site] = L::W(i) + d[i];

@@ -14,7 +14,7 @@ namespace lbm {
 struct LatticeOps {
   int Q, D;
   cudaError_t (*step)(int P, int FO, const void* fin, void* fout, const StepParams& p, int bx,
-                      bool overlap, cudaStream_t s);
+                      bool overlap, cudaStream_t s);  // p.solid set: FP64 / FP32 only
   cudaError_t (*init)(int P, int mode, const double* rho, const double* u, const double* T,
                       void* fout, unsigned* maxbits, int FO, const StepParams& p, cudaStream_t s);
   cudaError_t (*moments)(int P, const void* fin, double* rho, double* u, double* T, double* q,
@@ -62,6 +62,19 @@ struct Ops {
     cfg.attrs = attr;
     cfg.numAttrs = overlap ? 1 : 0;
     cudaError_t e = cudaSuccess;
+    if (p.solid) {
+#define LBM_SOLID_CASE(PP, FF)                                                                 \
+  case PP * 4 + FF:                                                                            \
+    e = cudaLaunchKernelEx(&cfg, k_step<L, PP, FF, true>, (const T<PP>*)fin, (T<PP>*)fout, p); \
+    break;
+      switch (P * 4 + FO) {
+        LBM_SOLID_CASE(0, 0) LBM_SOLID_CASE(0, 1) LBM_SOLID_CASE(0, 2) LBM_SOLID_CASE(0, 3)
+        LBM_SOLID_CASE(1, 0) LBM_SOLID_CASE(1, 1) LBM_SOLID_CASE(1, 2) LBM_SOLID_CASE(1, 3)
+        default: return cudaErrorInvalidValue;
+      }
+#undef LBM_SOLID_CASE
+      return e != cudaSuccess ? e : cudaGetLastError();
+    }
 #define LBM_STEP_CASE(PP, FF)                                                            \
   case PP * 4 + FF:                                                                      \
     e = cudaLaunchKernelEx(&cfg, k_step<L, PP, FF>, (const T<PP>*)fin, (T<PP>*)fout, p); \

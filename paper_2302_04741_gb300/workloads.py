@@ -175,6 +175,50 @@ def poiseuille(theta_b=1.0, theta_t=1.1, force_order=2, include_sigma=False, Lx=
                      + ("_sigma" if include_sigma else ""))
 
 
+def cylinders_parameters(theta_i, theta_o, L=250, ratio=5.0, Uc=0.3, Re=100.0, rho0=1.0,
+                         c=C_D2Q37):
+    """Parameters of the concentric-cylinder test (Sec. 3.2): outer radius
+    R_o = L c / 2, inner R_i = R_o / ratio, centre-line speed U_c = alpha (R_o
+    + R_i) / 2 (which fixes the angular speed alpha), Re = rho0 alpha (R_o^2 -
+    R_i^2) / (2 mu) (which fixes mu)."""
+    Ro = L * c / 2.0
+    Ri = Ro / ratio
+    alpha = Uc / (0.5 * (Ro + Ri))
+    mu = rho0 * alpha * (Ro * Ro - Ri * Ri) / (2.0 * Re)
+    return dict(Ro=Ro, Ri=Ri, alpha=alpha, mu=mu, rho0=rho0, theta_i=theta_i, theta_o=theta_o,
+                Uc=Uc, Re=Re, L=L, c=c)
+
+
+def cylinders(theta_i=1.0, theta_o=1.1, force_order=2, L=250, margin=3, precision=FP64, **kw):
+    """Heat transfer between concentric cylinders rotating together (Sec. 3.2),
+    in the co-rotating frame: static fluid under the centrifugal acceleration
+    g = alpha^2 R (radially outward) on an (L + 2 margin)^2 periodic D2Q37 grid.
+    Sites farther than R_o from the centre, or nearer than R_i, are solid walls
+    at theta_o and theta_i (a staircase); the margin keeps >= 3 solid rows
+    between the outer wall and the periodic edges.  Constant mu; starts from
+    rho = rho0, u = 0 and the conduction profile theta(R) ~ ln R."""
+    prm = cylinders_parameters(theta_i, theta_o, L=L, **kw)
+    n = L + 2 * margin
+    shape = (n, n, 1)
+    N = n * n
+    xx, yy, _ = _coords(shape)
+    cx = cy = 0.5 * (n - 1)
+    X, Y = prm["c"] * (xx - cx), prm["c"] * (yy - cy)
+    R = np.hypot(X, Y)
+    inner, outer = R < prm["Ri"], R > prm["Ro"]
+    solid = inner | outer
+    T_wall = np.where(inner, theta_i, theta_o)
+    Rc = np.clip(R, prm["Ri"], prm["Ro"])
+    T = theta_i + (theta_o - theta_i) * np.log(Rc / prm["Ri"]) / math.log(prm["Ro"] / prm["Ri"])
+    a2 = prm["alpha"] ** 2
+    field = np.stack([a2 * X, a2 * Y])
+    return dict(lattice=D2Q37, shape=shape, tau=1.0, mu=prm["mu"], precision=precision,
+                force_order=force_order, bc=(PERIODIC,) * 3, T_lo=(1.0,) * 3, T_hi=(1.0,) * 3,
+                g={"kind": G_FIELD, "field": field}, rho=np.full(N, prm["rho0"]),
+                u=np.zeros((2, N)), T=T, solid=solid.astype(np.uint8), T_wall=T_wall, radius=R,
+                params=prm, name=f"cylinders_{n}x{n}_theta{theta_i}-{theta_o}_N{force_order}")
+
+
 RAGGED_SIDES = (128, 192, 256, 384, 512)
 
 

@@ -28,6 +28,8 @@ def oracle_sim(w):
                          bc=w.get("bc", (0, 0, 0)), T_lo=w.get("T_lo", (1, 1, 1)),
                          T_hi=w.get("T_hi", (1, 1, 1)), mu=w.get("mu", 0.0),
                          include_sigma=w.get("include_sigma", False))
+    if w.get("solid") is not None:
+        s.set_solid(w["solid"], w["T_wall"])
     s.init(w["rho"], w["u"], w["T"])
     return s
 

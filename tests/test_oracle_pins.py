@@ -498,3 +498,64 @@ def test_sigma_bar_is_traceless(lat, shape):
     scale = np.max(np.abs(sig))
     assert scale > 1e-4
     assert np.max(np.abs(tr)) < 1e-13 * max(scale, 1.0)
+
+
+# ------------------------------------ solid sites (staircase diffuse walls)
+def annulus(n, r_in, r_out):
+    yy, xx = np.indices((n, n))
+    r = np.hypot(xx - (n - 1) / 2, yy - (n - 1) / 2).ravel()
+    return r, (r < r_in) | (r > r_out)
+
+
+def test_solid_walls_conserve_mass_and_keep_rest_state():
+    """Each fluid site re-emits through its wall links the mass it sent into
+    solid sites, so total fluid mass is constant to round-off; a fluid at
+    rest at the walls' temperature is a fixed point."""
+    n = 20
+    r, solid = annulus(n, 3, 8.5)
+    N = n * n
+    g = 1e-4 * (W.uniform(3, 5, 2 * N).reshape(2, N) - 0.5)
+    sim = make_sim(oracle.D2Q37, (n, n, 1), 0.7, g)
+    sim.set_solid(solid, np.where(r < 3, 1.1, 0.95))
+    rho, u, T = smooth_random_state(oracle.D2Q37, (n, n, 1), 6)
+    sim.init(rho, u, T)
+    fl = ~solid
+    m0 = sim.moments()[0][fl].sum()
+    sim.step(25)
+    rho1 = sim.moments()[0]
+    assert abs(rho1[fl].sum() - m0) < 1e-12 * m0
+    assert np.all(rho1[solid] == 0.0)
+    rest = make_sim(oracle.D2Q37, (n, n, 1), 0.7, np.zeros((2, N)))
+    rest.set_solid(solid, np.ones(N))
+    rest.init(np.ones(N), np.zeros((2, N)), np.ones(N))
+    f0 = rest.pulled()
+    rest.step(5)
+    np.testing.assert_allclose(rest.pulled()[:, fl], f0[:, fl], rtol=1e-14, atol=0)
+
+
+@pytest.mark.slow
+def test_solid_slabs_conduct_like_fourier():
+    """Two solid slabs (rows below 3 and above ny - 4) at 1.05 and 0.95: the
+    fluid between them relaxes to no flow, uniform pressure and a linear
+    temperature with q = -lambda dtheta/dy, lambda = c_p p (tau-hat - 1/2)."""
+    nx, ny, tau = 3, 30, 1.0
+    N = nx * ny
+    yy = np.repeat(np.arange(ny), nx)
+    solid = (yy < 3) | (yy >= ny - 3)
+    sim = make_sim(oracle.D2Q37, (nx, ny, 1), tau, np.zeros((2, N)))
+    sim.set_solid(solid, np.where(yy < 3, 1.05, 0.95))
+    sim.init(np.ones(N), np.zeros((2, N)), np.ones(N))
+    sim.step(4000)
+    rho, u, T, q = sim.moments()
+    col = lambda v: v.reshape(ny, nx)[:, 0]
+    T, p, qy = col(T), col(rho * T), col(q[1])
+    # the wall rows carry a steady layer of alternating u_y (6e-4 at the first
+    # fluid row, decaying ~3x per row); the bulk is still
+    bulk = slice(10, ny - 10)
+    assert np.max(np.abs(u.reshape(2, ny, nx)[:, bulk])) < 2e-6
+    assert np.max(np.abs(p[bulk] / p[bulk].mean() - 1)) < 1e-5
+    Tb = T[bulk]
+    slope = (Tb[-1] - Tb[0]) / (len(Tb) - 1)
+    assert slope < 0 and np.max(np.abs(np.diff(Tb, 2))) < 2e-3 * abs(slope)
+    lam = (2 + 2) / 2 * p[bulk].mean() * (tau - 0.5)
+    np.testing.assert_allclose(qy[bulk], -lam * slope / sim.c, rtol=1e-2)
