@@ -493,16 +493,17 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   }
   const size_t pb = sizeof(double) * 2 * lbm::NCONS * c->nblk_cons;
   if (cudaMalloc(&c->part, pb) != cudaSuccess || cudaMalloc(&c->bad, sizeof(unsigned) * c->nblk_cons) != cudaSuccess ||
-      cudaMalloc(&c->dres, sizeof(double) * (2 * lbm::NCONS + 1)) != cudaSuccess ||
+      cudaMalloc(&c->dres, sizeof(double) * (2 * lbm::NCONS + 2)) != cudaSuccess ||
       cudaMalloc(&c->dmax, sizeof(unsigned)) != cudaSuccess ||
-      cudaMallocHost(&c->hres, sizeof(double) * (2 * lbm::NCONS + 1)) != cudaSuccess) {
+      cudaMalloc(&c->ticket, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(c->ticket, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&c->hres, sizeof(double) * (2 * lbm::NCONS + 2)) != cudaSuccess) {
     cudaGetLastError();
     fail(c, LBM_ENOMEM, "cannot allocate reduction scratch");
     return bail(LBM_ENOMEM);
   }
-  c->bytes += pb + sizeof(unsigned) * c->nblk_cons + sizeof(double) * (2 * lbm::NCONS + 1) + sizeof(unsigned);
-  if (cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess || cudaMemset(c->derr, 0, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&c->herr, sizeof(int)) != cudaSuccess) {
+  c->bytes += pb + sizeof(unsigned) * c->nblk_cons + sizeof(double) * (2 * lbm::NCONS + 2) + 2 * sizeof(unsigned);
+  if (cudaMalloc(&c->derr, sizeof(int)) != cudaSuccess || cudaMemset(c->derr, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     fail(c, LBM_ENOMEM, "cannot allocate the error flag");
     return bail(LBM_ENOMEM);
@@ -663,13 +664,16 @@ int lbm_conserved(lbm_ctx* c, double* mass, double* mom, double* energy) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
   if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_conserved before lbm_init");
   LBM_CUDA(c, cudaSetDevice(c->device));
-  LBM_CUDA(c, c->ops->conserved(c->opt.precision, c->f[c->cur], c->part, c->bad, c->p, c->nblk_cons, c->stream));
-  lbm::k_conserved_final<<<1, 256, 0, c->stream>>>(c->part, c->bad, c->nblk_cons, c->dres);
-  LBM_CUDA(c, cudaGetLastError());
-  LBM_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * (2 * lbm::NCONS + 1), cudaMemcpyDeviceToHost, c->stream));
-  LBM_CUDA(c, cudaMemcpyAsync(c->herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  // one launch: block partials, then the last block's fixed-order final
+  // reduction written straight into the page-locked result when it is mapped
+  double* hview = device_view(c->hres);
+  LBM_CUDA(c, c->ops->conserved(c->opt.precision, c->f[c->cur], c->part, c->bad, c->ticket,
+                                hview ? hview : c->dres, c->derr, c->p, c->nblk_cons, c->stream));
+  if (!hview)
+    LBM_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, sizeof(double) * (2 * lbm::NCONS + 2),
+                                cudaMemcpyDeviceToHost, c->stream));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (*c->herr) {
+  if (c->hres[2 * lbm::NCONS + 1] != 0.0) {
     LBM_CUDA(c, cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
     return fail(c, LBM_ETIMEOUT, "a bounded device wait ran out in an earlier step; its results are void");
   }
@@ -850,8 +854,8 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->dmax);
   cudaFree(c->tmp);
   cudaFree(c->derr);
+  cudaFree(c->ticket);
   if (c->hres) cudaFreeHost(c->hres);
-  if (c->herr) cudaFreeHost(c->herr);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();
   delete c;

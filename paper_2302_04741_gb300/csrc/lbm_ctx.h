@@ -31,7 +31,8 @@ struct lbm_ctx {
   float* wall_th_f = nullptr;  // its float copy
   double* part = nullptr;      // conservation partials (2 * NCONS per block)
   unsigned* bad = nullptr;     // bad-site counts per block
-  double* dres = nullptr;      // final reduction result
+  double* dres = nullptr;      // final reduction result (when hres is not mapped)
+  unsigned* ticket = nullptr;  // last-block ticket of the conservation pass
   unsigned* dmax = nullptr;    // FP16 init: max |d/w| bits
   double* hres = nullptr;      // pinned host copy of the result
   double* tmp = nullptr;       // (2 + 2D) * N doubles, lazily allocated
@@ -45,7 +46,6 @@ struct lbm_ctx {
   size_t bytes = 0;
   int device = 0;
   int* derr = nullptr;         // device flag set by a bounded wait that ran out
-  int* herr = nullptr;         // pinned host copy
   bool use_tma = false;        // TMA-staged step kernel
   CUtensorMap tmap[2];         // tensor maps of f[0], f[1]
   int tma_grid = 0, tma_stages = 0;

@@ -645,41 +645,45 @@ __device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
 // Quantities reduced: 0 mass, 1..3 momentum, 4 energy; plus a count of bad sites.
 constexpr int NCONS = 5;
 
+// Block sum of per-thread values (plain doubles) with compensated adds, in a
+// fixed order: the values go to shared memory, then 8 threads per quantity
+// each sum a contiguous run of BS / 8 values, and one thread per quantity
+// merges those 8 partial sums.  (A shuffle tree makes every thread do the
+// compensated merges of every level on the FP64 pipe, which dominated this
+// otherwise light pass.)  Writes the (s, c) pair of each quantity and the
+// bad-site count of block `block`.
 template <int BS>
-__device__ __forceinline__ void block_reduce_store(KSum (&v)[NCONS], unsigned bad,
+__device__ __forceinline__ void block_reduce_store(const double (&v)[NCONS], unsigned bad,
                                                    double* __restrict__ part, unsigned* badcount,
                                                    int block) {
-  __shared__ double sh_s[BS / 32][NCONS], sh_c[BS / 32][NCONS];
+  static_assert(BS % 32 == 0 && BS >= 64, "block size");
+  constexpr int RUN = BS / 8;
+  __shared__ double sh_v[NCONS][BS];
+  __shared__ KSum sh_p[NCONS][8];
   __shared__ unsigned sh_bad[BS / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NCONS; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      KSum o{__shfl_down_sync(0xffffffffu, v[k].s, off), __shfl_down_sync(0xffffffffu, v[k].c, off)};
-      v[k] = ksum_merge(v[k], o);
-    }
-  }
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < NCONS; ++k) sh_v[k][tid] = v[k];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, off);
-  if (lane == 0) {
-    for (int k = 0; k < NCONS; ++k) {
-      sh_s[warp][k] = v[k].s;
-      sh_c[warp][k] = v[k].c;
-    }
-    sh_bad[warp] = bad;
+  if (lane == 0) sh_bad[warp] = bad;
+  __syncthreads();
+  if (tid < NCONS * 8) {
+    const int k = tid / 8, r = tid % 8;
+    KSum acc{0.0, 0.0};
+    for (int j = 0; j < RUN; ++j) acc = ksum_add(acc, sh_v[k][r * RUN + j]);
+    sh_p[k][r] = acc;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned b = 0;
-    for (int k = 0; k < NCONS; ++k) {
-      KSum acc{0.0, 0.0};
-      for (int w = 0; w < BS / 32; ++w) acc = ksum_merge(acc, KSum{sh_s[w][k], sh_c[w][k]});
-      part[(size_t)block * 2 * NCONS + 2 * k] = acc.s;
-      part[(size_t)block * 2 * NCONS + 2 * k + 1] = acc.c;
-    }
-    for (int w = 0; w < BS / 32; ++w) b += sh_bad[w];
-    badcount[block] = b;
+  if (tid < NCONS) {
+    KSum acc = sh_p[tid][0];
+    for (int r = 1; r < 8; ++r) acc = ksum_merge(acc, sh_p[tid][r]);
+    part[(size_t)block * 2 * NCONS + 2 * tid] = acc.s;
+    part[(size_t)block * 2 * NCONS + 2 * tid + 1] = acc.c;
+  }
+  if (tid == 0) {
+    unsigned b2 = 0;
+    for (int w = 0; w < BS / 32; ++w) b2 += sh_bad[w];
+    badcount[block] = b2;
   }
 }
 
@@ -688,21 +692,34 @@ __device__ __forceinline__ void block_reduce_store(KSum (&v)[NCONS], unsigned ba
 // site only the raw moments are needed, in the codec's arithmetic precision:
 // mass rho = 1 + drho, momentum rho u = c j + rho g / 2, energy
 // rho (|u|^2 + D theta) / 2 = (K + c j.g + rho |g|^2 / 2) / 2 with
-// K = D + c^2 k2 (mid-point values of R1, no division).  Each thread sums its
-// sites in double; the warp, block and final merges are compensated
+// K = D + c^2 k2 (mid-point values of R1, no division).  With a uniform g
+// these are linear in the per-site sums of drho, j and k2, so a thread sums
+// only those (in double) and forms its momentum and energy once; otherwise
+// it sums the per-site values.  The block and final merges are compensated
 // (two-sum).  The number of blocks is fixed by the caller, so the summation
 // order, and the result, are deterministic for a grid.  part:
 // gridDim.x * 2 * NCONS doubles, badcount: gridDim.x.
+//
+// ticket != nullptr: the last block to finish (by an atomic ticket) also
+// reduces all partials in block order into out (the k_conserved_final
+// layout, plus out[2 NCONS + 1] = *err, the bounded-wait error flag) and
+// resets the ticket; out may be mapped host memory.
 template <class L, int P>
 __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* __restrict__ fin,
                                                    double* __restrict__ part,
                                                    unsigned* __restrict__ badcount,
+                                                   unsigned* __restrict__ ticket,
+                                                   double* __restrict__ out,
+                                                   const int* __restrict__ err,
                                                    const StepParams p) {
   using R = typename Codec<P>::R;
   constexpr int Q = L::Q, D = L::D;
   const int ntx = (p.nx + 127) / 128;
   const int ntiles = ntx * p.ny * p.nz;
+  const bool uniform = p.gkind == G_UNIFORM;
   double acc[NCONS] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double sdrho = 0.0, sj[3] = {0.0, 0.0, 0.0}, sk2 = 0.0;
+  int count = 0;
   unsigned bad = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int xt = t % ntx, row = t / ntx;
@@ -714,31 +731,91 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
     R d[Q];
     if (p.solid) pull_solid<L, P, R>(fin, p, x, y, z, site, d);
     else pull<L, P, R>(fin, p, x, y, z, d);
-    double g[3];
-    site_force<D>(p, x, y, z, site, g);
+    R g[3];
+    site_force_r<D, R>(p, x, y, z, site, g);
     const RawMoments<L, R> r = raw_moments<L, R>(d);
-    const double rho = 1.0 + double(r.drho);
-    double jc[3], jg = 0.0, g2 = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      jc[a] = L::c * double(r.j[a]);
-      jg += jc[a] * g[a];
-      g2 += g[a] * g[a];
+    if (uniform) {
+      ++count;
+      sdrho += double(r.drho);
+      for (int a = 0; a < D; ++a) sj[a] += double(r.j[a]);
+      sk2 += double(r.k2);
+    } else {
+      const double rho = 1.0 + double(r.drho);
+      double jc[3], jg = 0.0, g2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        jc[a] = L::c * double(r.j[a]);
+        jg += jc[a] * double(g[a]);
+        g2 += double(g[a]) * double(g[a]);
+      }
+      acc[0] += rho;
+      for (int a = 0; a < D; ++a) acc[1 + a] += jc[a] + 0.5 * rho * double(g[a]);
+      acc[4] += 0.5 * (double(D) + L::c2 * double(r.k2) + jg + 0.5 * rho * g2);
     }
-    const double K = double(D) + L::c2 * double(r.k2);
-    const double e = 0.5 * (K + jg + 0.5 * rho * g2);
-    acc[0] += rho;
-    for (int a = 0; a < D; ++a) acc[1 + a] += jc[a] + 0.5 * rho * g[a];
-    acc[4] += e;
-    // D theta = (K - |c j|^2 / rho) / rho + g^2 / 4 in the codec's precision
-    const R rr = R(rho);
-    const R th = ((R(K) - R(jc[0] * jc[0] + jc[1] * jc[1] + jc[2] * jc[2]) / rr) / rr +
-                  R(0.25 * g2)) * R(1.0 / D);
-    const bool finite = isfinite(rho) && isfinite(e) && isfinite(th);
-    bad += (!finite || !(rho > 0.0) || !(th > R(0))) ? 1u : 0u;
+    // positivity check in the codec's precision:
+    // D theta = (K - |c j|^2 / rho) / rho + g^2 / 4, K = D + c^2 k2
+    const R rr = R(1) + r.drho;
+    const R K = R(D) + mul_c2<L, R>(r.k2);
+    const R j0 = mul_c<L, R>(r.j[0]), j1 = mul_c<L, R>(r.j[1]), j2 = mul_c<L, R>(r.j[2]);
+    const R th = ((K - (j0 * j0 + j1 * j1 + j2 * j2) / rr) / rr +
+                  R(0.25) * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2])) * R(1.0 / D);
+    const bool finite = isfinite(rr) && isfinite(K) && isfinite(th);
+    bad += (!finite || !(rr > R(0)) || !(th > R(0))) ? 1u : 0u;
   }
-  KSum v[NCONS];
-  for (int k = 0; k < NCONS; ++k) v[k] = KSum{acc[k], 0.0};
-  block_reduce_store<128>(v, bad, part, badcount, blockIdx.x);
+  if (uniform) {
+    const double g[3] = {p.g0[0], p.g0[1], D == 3 ? p.g0[2] : 0.0};
+    double jg = 0.0;
+    for (int a = 0; a < D; ++a) jg += L::c * sj[a] * g[a];
+    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const double mass = double(count) + sdrho;  // sum of rho = 1 + drho
+    acc[0] = mass;
+    for (int a = 0; a < D; ++a) acc[1 + a] = L::c * sj[a] + 0.5 * g[a] * mass;
+    acc[4] = 0.5 * (double(D) * count + L::c2 * sk2 + jg + 0.5 * g2 * mass);
+  }
+  block_reduce_store<128>(acc, bad, part, badcount, blockIdx.x);
+  if (!ticket) return;
+  // the last block to finish reduces every block's partials, in block order
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  __shared__ KSum fk[NCONS][128];
+  __shared__ unsigned fbs[128];
+  for (int k = 0; k < NCONS; ++k) {
+    KSum f{0.0, 0.0};
+    for (int blk = threadIdx.x; blk < (int)gridDim.x; blk += 128)
+      f = ksum_merge(f, KSum{__ldcg(part + (size_t)blk * 2 * NCONS + 2 * k),
+                             __ldcg(part + (size_t)blk * 2 * NCONS + 2 * k + 1)});
+    fk[k][threadIdx.x] = f;
+  }
+  unsigned fb = 0;
+  for (int blk = threadIdx.x; blk < (int)gridDim.x; blk += 128) fb += __ldcg(badcount + blk);
+  fbs[threadIdx.x] = fb;
+  __syncthreads();
+  __shared__ KSum fr[NCONS][8];
+  if (threadIdx.x < NCONS * 8) {  // 8 runs of 16 per quantity, then the runs
+    const int k = threadIdx.x / 8, r = threadIdx.x % 8;
+    KSum f = fk[k][r * 16];
+    for (int j = 1; j < 16; ++j) f = ksum_merge(f, fk[k][r * 16 + j]);
+    fr[k][r] = f;
+  }
+  __syncthreads();
+  if (threadIdx.x < NCONS) {
+    KSum f = fr[threadIdx.x][0];
+    for (int r = 1; r < 8; ++r) f = ksum_merge(f, fr[threadIdx.x][r]);
+    out[2 * threadIdx.x] = f.s;
+    out[2 * threadIdx.x + 1] = f.c;
+  }
+  if (threadIdx.x == 0) {
+    unsigned b2 = 0;
+    for (int j = 0; j < 128; ++j) b2 += fbs[j];
+    out[2 * NCONS] = double(b2);
+    out[2 * NCONS + 1] = err ? double(*(volatile const int*)err) : 0.0;
+    *ticket = 0u;
+  }
 }
 
 // Final pass: one block of 256 threads reduces the partials in a fixed order.

@@ -19,7 +19,9 @@ struct LatticeOps {
                       void* fout, unsigned* maxbits, int FO, const StepParams& p, cudaStream_t s);
   cudaError_t (*moments)(int P, const void* fin, double* rho, double* u, double* T, double* q,
                          int FO, const StepParams& p, cudaStream_t s);
+  // ticket != nullptr: the last block also reduces into out (see k_conserved)
   cudaError_t (*conserved)(int P, const void* fin, double* part, unsigned* bad,
+                           unsigned* ticket, double* out, const int* err,
                            const StepParams& p, int nblocks, cudaStream_t s);
   cudaError_t (*pulled)(int P, const void* fin, double* out, const StepParams& p, cudaStream_t s);
   cudaError_t (*state)(int P, int dir, void* f, double* io, const StepParams& p, cudaStream_t s);
@@ -117,11 +119,15 @@ struct Ops {
 
   // nblocks: blocks of the grid-stride conservation pass (partials written)
   static cudaError_t conserved(int P, const void* fin, double* part, unsigned* bad,
+                               unsigned* ticket, double* out, const int* err,
                                const StepParams& p, int nblocks, cudaStream_t s) {
     const dim3 g(nblocks), b(128);
-    if (P == P_FP64) k_conserved<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, part, bad, p);
-    else if (P == P_FP32S) k_conserved<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, part, bad, p);
-    else k_conserved<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, part, bad, p);
+    if (P == P_FP64)
+      k_conserved<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, part, bad, ticket, out, err, p);
+    else if (P == P_FP32S)
+      k_conserved<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, part, bad, ticket, out, err, p);
+    else
+      k_conserved<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, part, bad, ticket, out, err, p);
     return cudaGetLastError();
   }
 

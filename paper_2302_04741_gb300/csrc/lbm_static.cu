@@ -183,7 +183,8 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_of_current());
   const int nblocks = (int)(tiles < 4LL * nsm ? tiles : 4LL * nsm);
-  cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, p, nblocks, st);
+  cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, nullptr, nullptr, nullptr, p,
+                                 nblocks, st);
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "conservation kernel launch failed", e);
   lbm::k_conserved_final<<<1, 256, 0, st>>>(s->part, s->bad, nblocks, s->res);
   e = cudaGetLastError();
