@@ -642,6 +642,18 @@ __device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
   return r;
 }
 
+// Compensated (Neumaier) running sum in the arithmetic type R of a kernel.
+template <class R>
+struct RSum {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R v) {
+    const R t = s + v;
+    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
 // Quantities reduced: 0 mass, 1..3 momentum, 4 energy; plus a count of bad sites.
 constexpr int NCONS = 5;
 
@@ -704,8 +716,13 @@ __device__ __forceinline__ void block_reduce_store(const double (&v)[NCONS], uns
 // reduces all partials in block order into out (the k_conserved_final
 // layout, plus out[2 NCONS + 1] = *err, the bounded-wait error flag) and
 // resets the ticket; out may be mapped host memory.
+// Resident 128-thread blocks per SM the conservation pass is compiled for
+// (its grid is 4 blocks per SM; LBM_CONSERVED_BLOCKS is a tuning hook).
+#ifndef LBM_CONSERVED_BLOCKS
+#define LBM_CONSERVED_BLOCKS 4
+#endif
 template <class L, int P>
-__global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* __restrict__ fin,
+__global__ void __launch_bounds__(128, LBM_CONSERVED_BLOCKS) k_conserved(const typename Codec<P>::T* __restrict__ fin,
                                                    double* __restrict__ part,
                                                    unsigned* __restrict__ badcount,
                                                    unsigned* __restrict__ ticket,
@@ -718,7 +735,9 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
   const int ntiles = ntx * p.ny * p.nz;
   const bool uniform = p.gkind == G_UNIFORM;
   double acc[NCONS] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  double sdrho = 0.0, sj[3] = {0.0, 0.0, 0.0}, sk2 = 0.0;
+  // uniform force: per-thread compensated sums in the codec's precision (no
+  // FP64 work per site)
+  RSum<R> sdrho{}, sj[3] = {}, sk2{};
   int count = 0;
   unsigned bad = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -736,9 +755,9 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
     const RawMoments<L, R> r = raw_moments<L, R>(d);
     if (uniform) {
       ++count;
-      sdrho += double(r.drho);
-      for (int a = 0; a < D; ++a) sj[a] += double(r.j[a]);
-      sk2 += double(r.k2);
+      sdrho.add(r.drho);
+      for (int a = 0; a < D; ++a) sj[a].add(r.j[a]);
+      sk2.add(r.k2);
     } else {
       const double rho = 1.0 + double(r.drho);
       double jc[3], jg = 0.0, g2 = 0.0;
@@ -763,13 +782,16 @@ __global__ void __launch_bounds__(128) k_conserved(const typename Codec<P>::T* _
   }
   if (uniform) {
     const double g[3] = {p.g0[0], p.g0[1], D == 3 ? p.g0[2] : 0.0};
-    double jg = 0.0;
-    for (int a = 0; a < D; ++a) jg += L::c * sj[a] * g[a];
+    double J[3] = {0.0, 0.0, 0.0}, jg = 0.0;
+    for (int a = 0; a < D; ++a) {
+      J[a] = sj[a].value();
+      jg += L::c * J[a] * g[a];
+    }
     const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    const double mass = double(count) + sdrho;  // sum of rho = 1 + drho
+    const double mass = double(count) + sdrho.value();  // sum of rho = 1 + drho
     acc[0] = mass;
-    for (int a = 0; a < D; ++a) acc[1 + a] = L::c * sj[a] + 0.5 * g[a] * mass;
-    acc[4] = 0.5 * (double(D) * count + L::c2 * sk2 + jg + 0.5 * g2 * mass);
+    for (int a = 0; a < D; ++a) acc[1 + a] = L::c * J[a] + 0.5 * g[a] * mass;
+    acc[4] = 0.5 * (double(D) * count + L::c2 * sk2.value() + jg + 0.5 * g2 * mass);
   }
   block_reduce_store<128>(acc, bad, part, badcount, blockIdx.x);
   if (!ticket) return;
