@@ -142,7 +142,13 @@ typedef struct {
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_PLAIN = 1, LBM_KERNEL_TMA = 2,
        LBM_KERNEL_PREFETCH = 3 /* persistent; each thread prefetches its next tile's
                                   populations into shared memory with cp.async while
-                                  colliding the current one (FP32-shifted only) */ };
+                                  colliding the current one (FP32-shifted only) */,
+       LBM_KERNEL_WAVE = 4     /* several steps per launch: persistent blocks take
+                                  (step, line, tile) items in step-major order and
+                                  wait, with bounded polls, until the 3 lines on each
+                                  side finished the previous step; FP32-shifted and
+                                  FP16-scaled storage, no sigma-bar terms; results
+                                  identical to the plain kernel */ };
 
 /* Fills *opt with the defaults: FP64, force_order 2, no sigma, fully periodic,
  * wall temperatures 1, NULL stream, library block shape, no graph. */

@@ -27,7 +27,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ETIMEOUT, LBM_ESTA
 LBM_G_UNIFORM, LBM_G_SINE, LBM_G_FIELD = 0, 1, 2
 LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SCALED = 0, 1, 2
 LBM_PERIODIC, LBM_BOUNCE_BACK, LBM_THERMAL_WALL = 0, 1, 2
-LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_TMA, LBM_KERNEL_PREFETCH = 0, 1, 2, 3
+LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_TMA, LBM_KERNEL_PREFETCH, LBM_KERNEL_WAVE = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
                 -4: "LBM_EUNSTABLE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_EIO"}
 

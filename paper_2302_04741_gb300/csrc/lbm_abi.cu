@@ -208,6 +208,37 @@ bool make_tensor_maps(lbm_ctx* c, std::string* why) {
 bool setup_step_kernel(lbm_ctx* c, std::string* why) {
   c->use_tma = false;
   c->use_async = false;
+  c->use_wave = false;
+  if (c->opt.kernel == LBM_KERNEL_WAVE) {
+    if (c->opt.precision != LBM_FP32_SHIFTED && c->opt.precision != LBM_FP16_SCALED) {
+      *why = "the wavefront kernel serves FP32-shifted and FP16-scaled storage";
+      return false;
+    }
+    if (c->fo > 2) {
+      *why = "the sigma-bar terms run in the plain step kernel only";
+      return false;
+    }
+    int bps = 0, nsm = 0;
+    cudaError_t e = c->ops->wave_occupancy(c->opt.precision, c->fo, &bps);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess || bps < 1) {
+      cudaGetLastError();
+      *why = "the wavefront kernel does not fit on this device";
+      return false;
+    }
+    const int nA = c->D == 2 ? c->ny : c->nz;
+    if (!c->wave_sync) {
+      if (cudaMalloc(&c->wave_sync, sizeof(unsigned) * (1 + (size_t)nA)) != cudaSuccess) {
+        cudaGetLastError();
+        *why = "cannot allocate the wavefront counters";
+        return false;
+      }
+      c->bytes += sizeof(unsigned) * (1 + (size_t)nA);
+    }
+    c->wave_grid = bps * nsm;
+    c->use_wave = true;
+    return true;
+  }
   if (c->opt.kernel == LBM_KERNEL_PREFETCH) {
     if (c->opt.precision != LBM_FP32_SHIFTED) {
       *why = "the prefetching kernel serves FP32-shifted storage only";
@@ -253,6 +284,24 @@ bool setup_step_kernel(lbm_ctx* c, std::string* why) {
   return ok || c->opt.kernel == LBM_KERNEL_AUTO;
 }
 
+// n steps of the wavefront kernel: launches of at most as many steps as keep
+// the item count below 2^31, each after zeroing its counters.
+int launch_wave_steps(lbm_ctx* c, int n) {
+  const int nA = c->D == 2 ? c->ny : c->nz;
+  const long long per_step = (long long)((c->nx + lbm::WAVE_BX - 1) / lbm::WAVE_BX) * c->ny * c->nz;
+  const int kmax = (int)std::max<long long>(1, ((1LL << 31) - 1) / per_step);
+  while (n > 0) {
+    const int k = std::min(n, kmax);
+    LBM_CUDA(c, cudaMemsetAsync(c->wave_sync, 0, sizeof(unsigned) * (1 + (size_t)nA), c->stream));
+    cudaError_t e = c->ops->step_wave(c->opt.precision, c->fo, c->f[c->cur], c->f[c->cur ^ 1], c->p,
+                                      k, c->wave_sync, c->wave_grid, c->stream);
+    if (e != cudaSuccess) return fail(c, LBM_ECUDA, "wavefront launch failed: %s", cudaGetErrorString(e));
+    c->cur ^= k & 1;
+    n -= k;
+  }
+  return LBM_OK;
+}
+
 int launch_one_step(lbm_ctx* c) {
   cudaError_t e;
   if (c->use_tma)
@@ -277,7 +326,9 @@ int build_graph(lbm_ctx* c, int par) {
   c->cur = par;
   LBM_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   int rc = LBM_OK;
-  for (int k = 0; k < c->opt.graph_steps && rc == LBM_OK; ++k) rc = launch_one_step(c);
+  if (c->use_wave) rc = launch_wave_steps(c, c->opt.graph_steps);
+  else
+    for (int k = 0; k < c->opt.graph_steps && rc == LBM_OK; ++k) rc = launch_one_step(c);
   cudaError_t e = cudaStreamEndCapture(c->stream, &g);
   c->cur = saved;
   if (rc != LBM_OK) {
@@ -344,7 +395,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   if (o.force_order < 0 || o.force_order > 2)
     return fail(nullptr, LBM_EINVAL, "force_order must be 0, 1 or 2 (got %d)", o.force_order);
   if (o.include_sigma && o.force_order == 2 &&
-      (o.kernel == LBM_KERNEL_TMA || o.kernel == LBM_KERNEL_PREFETCH))
+      (o.kernel == LBM_KERNEL_TMA || o.kernel == LBM_KERNEL_PREFETCH || o.kernel == LBM_KERNEL_WAVE))
     return fail(nullptr, LBM_EINVAL, "the sigma-bar terms run in the plain step kernel only");
   const int n[3] = {nx, ny, nz};
   int wall = lbm::W_NONE;
@@ -375,7 +426,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     return fail(nullptr, LBM_EINVAL, "block_x must be a multiple of 32 in [32, 256] (got %d)", o.block_x);
   if (o.graph_steps < 0 || o.graph_steps % 2)
     return fail(nullptr, LBM_EINVAL, "graph_steps must be even and >= 0 (got %d)", o.graph_steps);
-  if (o.kernel < LBM_KERNEL_AUTO || o.kernel > LBM_KERNEL_PREFETCH)
+  if (o.kernel < LBM_KERNEL_AUTO || o.kernel > LBM_KERNEL_WAVE)
     return fail(nullptr, LBM_EINVAL, "unknown kernel choice %d", o.kernel);
   if (!(o.mu >= 0.0) || !std::isfinite(o.mu)) return fail(nullptr, LBM_EINVAL, "mu must be >= 0");
   if (o.overlap_steps < -1 || o.overlap_steps > 1)
@@ -576,7 +627,8 @@ int lbm_set_solid(lbm_ctx* c, const unsigned char* solid, const double* T_wall) 
   if (c->p.wall != lbm::W_NONE) return fail(c, LBM_EINVAL, "solid sites need all axes periodic");
   if (c->opt.precision == LBM_FP16_SCALED)
     return fail(c, LBM_EINVAL, "solid sites run with FP64 or FP32-shifted storage");
-  if (c->use_tma || c->use_async) return fail(c, LBM_EINVAL, "solid sites run in the plain step kernel");
+  if (c->use_tma || c->use_async || c->use_wave)
+    return fail(c, LBM_EINVAL, "solid sites run in the plain step kernel");
   LBM_CUDA(c, cudaSetDevice(c->device));
   const size_t N = (size_t)c->N;
   std::vector<unsigned char> s(N);
@@ -624,6 +676,11 @@ int lbm_step(lbm_ctx* c, int n) {
     }
     LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
     left -= G;
+  }
+  if (c->use_wave && left > 0) {
+    int rc = launch_wave_steps(c, left);
+    if (rc) return rc;
+    left = 0;
   }
   for (; left > 0; --left) {
     int rc = launch_one_step(c);
@@ -745,6 +802,7 @@ long long lbm_step_count(const lbm_ctx* c) { return c ? c->steps : 0; }
 
 int lbm_step_kernel(const lbm_ctx* c) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (c->use_wave) return LBM_KERNEL_WAVE;
   return c->use_tma ? LBM_KERNEL_TMA : (c->use_async ? LBM_KERNEL_PREFETCH : LBM_KERNEL_PLAIN);
 }
 
@@ -855,6 +913,7 @@ void lbm_destroy(lbm_ctx* c) {
   cudaFree(c->tmp);
   cudaFree(c->derr);
   cudaFree(c->ticket);
+  cudaFree(c->wave_sync);
   if (c->hres) cudaFreeHost(c->hres);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   cudaGetLastError();

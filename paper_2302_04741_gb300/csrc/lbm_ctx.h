@@ -51,6 +51,9 @@ struct lbm_ctx {
   int tma_grid = 0, tma_stages = 0;
   bool use_async = false;      // prefetching persistent step kernel
   int async_grid = 0;
+  bool use_wave = false;       // several steps per launch (wavefront order)
+  int wave_grid = 0;
+  unsigned* wave_sync = nullptr;  // item counter + per-line done counts
   lbm_batch* batch = nullptr;  // batch this context is a member of
   std::string err;
 };

@@ -183,6 +183,7 @@ template <> struct Codec<P_FP64> {
   template <class L, int I>
   __device__ __forceinline__ static T encode(R d, const StepParams&) { return d + L::W(I); }
   __device__ __forceinline__ static T load(const T* p) { return __ldg(p); }
+  __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
 };
 
 template <> struct Codec<P_FP32S> {
@@ -193,6 +194,7 @@ template <> struct Codec<P_FP32S> {
   template <class L, int I>
   __device__ __forceinline__ static T encode(R d, const StepParams&) { return d; }
   __device__ __forceinline__ static T load(const T* p) { return __ldg(p); }
+  __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
 };
 
 template <> struct Codec<P_FP16S> {
@@ -209,7 +211,17 @@ template <> struct Codec<P_FP16S> {
     return __float2half_rn(d * (iw * p.h_scale));
   }
   __device__ __forceinline__ static T load(const T* p) { return __ldg(p); }
+  __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
 };
+
+// Population load through the read-only path, or (CG) from L2 only: for a
+// kernel that reads what other blocks of the same launch wrote (the
+// read-only and L1 paths may hold stale lines).
+template <class C, bool CG>
+__device__ __forceinline__ typename C::T ldpop(const typename C::T* p) {
+  if constexpr (CG) return C::load_cg(p);
+  else return C::load(p);
+}
 
 // ------------------------------------------------------------ body force
 template <class R>

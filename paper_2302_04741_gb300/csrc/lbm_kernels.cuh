@@ -63,7 +63,7 @@ __device__ __forceinline__ void site_force_r(const StepParams& p, int x, int y, 
 
 // Pull of all Q populations of site (x, y, z) with the boundary rules, decoded
 // to deviations in type RR.  The wall axis is the last axis (y in 2-D, z in 3-D).
-template <class L, int P, class RR>
+template <class L, int P, class RR, bool CG = false>
 __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fin,
                                      const StepParams& p, int x, int y, int z, RR (&d)[L::Q]) {
   using C = Codec<P>;
@@ -85,7 +85,7 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
       constexpr int i = I;
       constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
       const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
-      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + off), p));
+      d[i] = RR(C::template decode<L, i>(ldpop<C, CG>(fin + i * N + off), p));
     });
     return;
   }
@@ -105,7 +105,7 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
         if constexpr (eA != 0) {
           const bool leaves = side == 0 ? (eA < 0 && r + eA < 0) : (eA > 0 && r - eA < 0);
           if (leaves)
-            sum += RR(C::template decode<L, j>(C::load(fin + j * N + colbase + row * lineA), p));
+            sum += RR(C::template decode<L, j>(ldpop<C, CG>(fin + j * N + colbase + row * lineA), p));
         }
       });
     }
@@ -118,11 +118,11 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
     const int sA = a - eA;
     if (sA >= 0 && sA < nA) {
       const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
-      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + off), p));
+      d[i] = RR(C::template decode<L, i>(ldpop<C, CG>(fin + i * N + off), p));
     } else if (p.wall == W_BOUNCE) {
       constexpr int io = opposite<i>();
       const int mA = side == 0 ? eA - 1 - a : 2 * nA - 1 - sA;
-      d[i] = RR(C::template decode<L, io>(C::load(fin + io * N + colbase + mA * lineA), p));
+      d[i] = RR(C::template decode<L, io>(ldpop<C, CG>(fin + io * N + colbase + mA * lineA), p));
     } else {
       d[i] = fma(rm1, RR(p.fw[side][i]), RR(p.fwd[side][i]));
     }
@@ -197,7 +197,7 @@ __device__ __forceinline__ void pull_solid(const typename Codec<P>::T* __restric
 // source offset relative to the thread's own site, i*N + (row / plane shift)
 // - e_ix, is the same for the whole block (rows wrap only through the block's
 // y, z), so addresses are a per-thread base plus block-uniform offsets.
-template <class L, int P, class RR>
+template <class L, int P, class RR, bool CG = false>
 __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __restrict__ fsite,
                                               const StepParams& p, int y, int z,
                                               RR (&d)[L::Q]) {
@@ -214,7 +214,7 @@ __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __rest
     constexpr int i = I;
     constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
     const long long off = i * N + dz[ez + 3] + dy[ey + 3] - ex;
-    d[i] = RR(C::template decode<L, i>(C::load(fsite + off), p));
+    d[i] = RR(C::template decode<L, i>(ldpop<C, CG>(fsite + off), p));
   });
 }
 
@@ -350,6 +350,15 @@ constexpr int min_blocks() {
   return P == P_FP64 ? 1 : (L::Q > 37 ? 2 : LBM_FLOAT_D2Q37_BLOCKS);
 }
 
+// Line of the wall axis a block works on.  With walls, the six wall rows
+// (whose pull gathers the wall sums and is slower) take the first six block
+// indices along that axis, so they start with the first wave instead of
+// forming the last blocks of the launch; the bulk rows follow in order.
+__device__ __forceinline__ int wall_rows_first(int b, int n, bool walls) {
+  if (!walls) return b;
+  return b < 3 ? b : (b < 6 ? n - 6 + b : b - 3);
+}
+
 // SOLID: the grid has solid sites (they are skipped; their fluid neighbours
 // take the diffuse-wall pull).
 template <class L, int P, int FO, bool SOLID = false>
@@ -359,7 +368,9 @@ __global__ void __launch_bounds__(256, min_blocks<L, P>())
   using R = typename Codec<P>::R;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const bool walls = p.wall != W_NONE;
+  const int y = L::D == 2 ? wall_rows_first(blockIdx.y, p.ny, walls) : (int)blockIdx.y;
+  const int z = L::D == 3 ? wall_rows_first(blockIdx.z, p.nz, walls) : (int)blockIdx.z;
   const int site = (z * p.ny + y) * p.nx + x;
   if constexpr (SOLID) {
     if (__ldg(p.solid + site)) return;

@@ -7,6 +7,7 @@
 #include "lbm_async.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_tma.cuh"
+#include "lbm_wave.cuh"
 
 namespace lbm {
 
@@ -38,6 +39,11 @@ struct LatticeOps {
   cudaError_t (*batch_occupancy)(int P, int FO, int spt, int bx, int* blocks_per_sm);
   cudaError_t (*batch_step)(int P, int FO, int spt, const BatchGrid* grids, const int* prefix,
                             const int* header, int k, int grid, int bx, cudaStream_t s);
+  // several steps in one persistent launch (FP32-shifted and FP16-scaled
+  // storage; force orders 0..2); sync: 1 + n_lines zeroed words
+  cudaError_t (*wave_occupancy)(int P, int FO, int* blocks_per_sm);
+  cudaError_t (*step_wave)(int P, int FO, void* f0, void* f1, const StepParams& p, int nsteps,
+                           unsigned* sync, int grid, cudaStream_t s);
 };
 
 inline dim3 row_grid(const StepParams& p, int bx) {
@@ -221,6 +227,27 @@ struct Ops {
     return cudaErrorInvalidValue;
   }
 
+  static cudaError_t wave_occupancy(int P, int FO, int* bps) {
+#define LBM_WOCC(PP, FF)                                                                         \
+  if (P == PP && FO == FF)                                                                       \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_step_wave<L, PP, FF>, WAVE_BX, 0);
+    LBM_WOCC(1, 0) LBM_WOCC(1, 1) LBM_WOCC(1, 2) LBM_WOCC(2, 0) LBM_WOCC(2, 1) LBM_WOCC(2, 2)
+#undef LBM_WOCC
+    return cudaErrorInvalidValue;
+  }
+
+  static cudaError_t step_wave(int P, int FO, void* f0, void* f1, const StepParams& p, int nsteps,
+                               unsigned* sync, int grid, cudaStream_t s) {
+#define LBM_WSTEP(PP, FF)                                                                      \
+  if (P == PP && FO == FF) {                                                                   \
+    k_step_wave<L, PP, FF><<<grid, WAVE_BX, 0, s>>>((T<PP>*)f0, (T<PP>*)f1, p, nsteps, sync);  \
+    return cudaGetLastError();                                                                 \
+  }
+    LBM_WSTEP(1, 0) LBM_WSTEP(1, 1) LBM_WSTEP(1, 2) LBM_WSTEP(2, 0) LBM_WSTEP(2, 1) LBM_WSTEP(2, 2)
+#undef LBM_WSTEP
+    return cudaErrorInvalidValue;
+  }
+
   static size_t async_smem(int bx) { return 2 * (size_t)L::Q * bx * sizeof(float); }
 
   static cudaError_t async_occupancy(int FO, int bx, int* bps) {
@@ -252,7 +279,7 @@ struct Ops {
   static LatticeOps table() {
     return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state,
                       &tma_smem, &tma_prepare, &step_tma, &async_occupancy, &step_async,
-                      &batch_occupancy, &batch_step};
+                      &batch_occupancy, &batch_step, &wave_occupancy, &step_wave};
   }
 };
 

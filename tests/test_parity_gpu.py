@@ -486,3 +486,38 @@ def test_prefetch_kernel_bitwise_equals_plain(case, block_x):
     a.step(7)
     b.step(7)
     np.testing.assert_array_equal(a.get_state(), b.get_state())
+
+
+WAVE_CASES = TMA_CASES + [("d2-periodic-y-short", 0, (96, 7, 1), (0, 0, 0))]
+
+
+@pytest.mark.parametrize("steps,graph", [(7, 0), (12, 4)])
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("case", WAVE_CASES, ids=[c[0] for c in WAVE_CASES])
+def test_wave_kernel_bitwise_equals_plain(case, precision, steps, graph):
+    """Several steps per launch (wavefront order) give exactly the plain
+    kernel's state, with walls or periodic wrap on the last axis, odd step
+    counts and graph replay."""
+    _, lat, shape, bc = case
+    w = workload(lat, shape, seed=21, precision=precision, bc=bc, force_order=2,
+                 T_lo=(1.0, 1.05, 1.05), T_hi=(1.0, 0.96, 0.96))
+    a = lbm.Sim(w, kernel=lbm.LBM_KERNEL_WAVE, graph_steps=graph).init()
+    assert lbm.lbm_step_kernel(a.ctx) == lbm.LBM_KERNEL_WAVE
+    b = lbm.Sim(w, kernel=lbm.LBM_KERNEL_PLAIN).init()
+    a.step(steps)
+    b.step(steps)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+    assert a.conserved()[0] == lbm.LBM_OK  # no bounded wait ran out
+    a.step(3)
+    b.step(3)
+    np.testing.assert_array_equal(a.populations(), b.populations())
+
+
+def test_wave_kernel_rejections():
+    w = workload(0, (64, 12, 1), precision=0)
+    with pytest.raises(lbm.LbmError):
+        lbm.Sim(w, kernel=lbm.LBM_KERNEL_WAVE)
+    w = workload(0, (64, 12, 1), precision=1)
+    w["include_sigma"] = True
+    with pytest.raises(lbm.LbmError):
+        lbm.Sim(w, kernel=lbm.LBM_KERNEL_WAVE)
