@@ -541,6 +541,71 @@ __device__ __forceinline__ HeatMoments<L> heat_moments(const double (&d)[L::Q]) 
   return h;
 }
 
+// The same raw moments from float deviations without FP64 arithmetic: each
+// moment is a float pair s + c, the pair sums d_+ +- d_- are split exactly
+// (Knuth's two-sum), products by the small integer weights keep their FMA
+// residual, and every rounding error goes into c.  The result equals the
+// FP64 sum to a few units in 2^-48 of the terms' magnitude.
+struct FF {
+  float s = 0.f, c = 0.f;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// acc += K (hi + lo) for a compile-time integer K
+template <int K>
+__device__ __forceinline__ void ff_mac(FF& acc, float hi, float lo) {
+  if constexpr (K != 0) {
+    const float p = float(K) * hi;
+    const float pe = fmaf(float(K), hi, -p);
+    float t, e;
+    two_sum(acc.s, p, t, e);
+    acc.s = t;
+    acc.c += e + pe + float(K) * lo;
+  }
+}
+
+template <class L>
+__device__ __forceinline__ HeatMoments<L> heat_moments_ff(const float (&d)[L::Q]) {
+  constexpr int NP = (L::Q - 1) / 2;
+  FF m0, m1[3], m2[6], m3[3];
+  m0.s = d[0];
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    constexpr int ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
+    constexpr int e2 = ex * ex + ey * ey + ez * ez;
+    float sh, sl, ah, al;
+    two_sum(d[ip], d[im], sh, sl);
+    two_sum(d[ip], -d[im], ah, al);
+    ff_mac<1>(m0, sh, sl);
+    ff_mac<ex>(m1[0], ah, al);
+    ff_mac<ey>(m1[1], ah, al);
+    ff_mac<ex * ex>(m2[0], sh, sl);
+    ff_mac<ey * ey>(m2[1], sh, sl);
+    ff_mac<ex * ey>(m2[3], sh, sl);
+    ff_mac<e2 * ex>(m3[0], ah, al);
+    ff_mac<e2 * ey>(m3[1], ah, al);
+    if constexpr (L::D == 3) {
+      ff_mac<ez>(m1[2], ah, al);
+      ff_mac<ez * ez>(m2[2], sh, sl);
+      ff_mac<ex * ez>(m2[4], sh, sl);
+      ff_mac<ey * ez>(m2[5], sh, sl);
+      ff_mac<e2 * ez>(m3[2], ah, al);
+    }
+  });
+  HeatMoments<L> h;
+  auto v = [](const FF& f) { return double(f.s) + double(f.c); };
+  h.m0 = v(m0);
+  for (int a = 0; a < 3; ++a) {
+    h.m1[a] = v(m1[a]);
+    h.m3[a] = v(m3[a]);
+  }
+  for (int k = 0; k < 6; ++k) h.m2[k] = v(m2[k]);
+  return h;
+}
+
 // Symmetric 3x3 (xx, yy, zz, xy, xz, yz) times a vector.
 __device__ __forceinline__ void sym_mul(const double (&S)[6], const double (&v)[3], double (&o)[3]) {
   o[0] = S[0] * v[0] + S[3] * v[1] + S[4] * v[2];
@@ -568,12 +633,20 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
     }
     return;
   }
-  double d[Q];
-  if (p.solid) pull_solid<L, P, double>(fin, p, x, y, z, site, d);
-  else pull<L, P, double>(fin, p, x, y, z, d);
+  HeatMoments<L> h;
+  if (P != P_FP64 && !p.solid) {
+    // float storage: the deviations are exact floats; sum them without FP64
+    float d[Q];
+    pull<L, P, float>(fin, p, x, y, z, d);
+    h = heat_moments_ff<L>(d);
+  } else {
+    double d[Q];
+    if (p.solid) pull_solid<L, P, double>(fin, p, x, y, z, site, d);
+    else pull<L, P, double>(fin, p, x, y, z, d);
+    h = heat_moments<L>(d);
+  }
   double g[3];
   site_force<D>(p, x, y, z, site, g);
-  const HeatMoments<L> h = heat_moments<L>(d);
   // mid-point state (R1), as in the step kernel
   const double c = L::c, c2 = L::c2;
   const double r = 1.0 + h.m0, ir = 1.0 / r;
