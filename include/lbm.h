@@ -177,8 +177,10 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
  * second-order scheme, Sec. 2) at the slots the next pull reads, so that
  * lbm_moments right after lbm_init returns the given fields (exactly up to
  * round-off for periodic and bounce-back boundaries).  rho: N, u: D*N,
- * T: N, doubles, host or device.  For LBM_FP16_SCALED this also fixes the
- * grid's scale.  Resets the step counter. */
+ * T: N, doubles, host or device (page-locked host arrays are read in place
+ * by the kernel; with any host array the call returns after the state is
+ * written, so the arrays may be reused at once).  For LBM_FP16_SCALED this
+ * also fixes the grid's scale.  Resets the step counter. */
 int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *T);
 
 /* Marks solid sites: walls of any shape as a staircase of sites (the
@@ -205,7 +207,9 @@ int lbm_step(lbm_ctx *ctx, int n);
  * u (D*N) = sum f~ xi / rho + g/2, T (N) = theta, and the heat flux q (D*N),
  * q = 1/2 (1 - 1/(2 tau)) sum_i (f~_i - f0_i + F_i/2) |xi_i - u|^2 (xi_i - u)
  * (the physical non-equilibrium part, Sec. 2).  Any output may be NULL.
- * Host or device pointers.  Synchronises the stream. */
+ * Host or device pointers; page-locked host outputs are written in place by
+ * the kernel over the host link (no staging copy), pageable ones through a
+ * device buffer.  Synchronises the stream. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *q);
 
 /* Global sums over the grid, in double with compensated (two-sum) block
