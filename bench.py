@@ -170,12 +170,26 @@ def dist_info():
 
 
 # --------------------------------------------------------------- the oracle arm
-def oracle_rate(w, steps, warmup, budget_s=None):
-    """MLUPS of the FP64 CPU oracle on workload w (host cores)."""
+def cpu_model():
+    """The host CPU's model name (or architecture) for the baseline record."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_rate(w, steps, warmup, budget_s=None, threads=None):
+    """MLUPS of the FP64 CPU oracle on workload w (host cores; threads=None:
+    all of them)."""
     import oracle
     from paper_2302_04741_gb300 import workloads as W
 
-    oracle.set_threads(os.cpu_count() or 1)
+    oracle.set_threads(threads or os.cpu_count() or 1)
     g = W.g_field_array(w["lattice"], w["shape"], w["g"])
     s = oracle.OracleSim(w["lattice"], *w["shape"], w["tau"], g, force_order=w["force_order"],
                          bc=w["bc"], T_lo=w["T_lo"], T_hi=w["T_hi"])
@@ -484,8 +498,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mlups, steps, dt, cores = oracle_rate(W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP64),
                                               40, 0, budget_s=12.0)
+        m1, s1, d1, _ = oracle_rate(W.rayleigh_benard(nx=256, ny=128, precision=W.FP64),
+                                    40, 0, budget_s=4.0, threads=1)
         cpu = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle, full {nx}x{ny} grid, {steps} LBM steps ({dt:.1f} s)"}
+               "sample": f"FP64 oracle, full {nx}x{ny} grid, {steps} LBM steps ({dt:.1f} s)",
+               "single_thread": {"value": m1, "unit": "MLUPS",
+                                 "sample": f"256x128 grid of the same workload, {s1} steps ({d1:.1f} s)"},
+               "cpu_model": cpu_model()}
 
     if rank == 0:
         line = {
