@@ -338,16 +338,22 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
 }
 
 // Resident 256-thread blocks per SM the register cap is sized for: float
-// D2Q37 kernels fit 85 registers (3 blocks) without spilling, float D3Q39
-// kernels need up to 128 (2 blocks); FP64 kernels keep their registers.
-// LBM_FLOAT_D2Q37_BLOCKS overrides the D2Q37 float value at build time (a
-// tuning hook: 4 caps at 64 registers and accepts a small spill).
+// kernels fit 85 registers (3 blocks) -- D2Q37 without spilling, D3Q39 with
+// at most 24 B of spill per thread, which measured 7-10 % faster than its
+// 128-register, 2-block variant (the batch kernel's two-sites-per-thread
+// variants spill more; its tuner measures both); FP64 kernels keep their
+// registers.
+// LBM_FLOAT_D2Q37_BLOCKS and LBM_FLOAT_D3Q39_BLOCKS override the float values
+// at build time (tuning hooks).
 #ifndef LBM_FLOAT_D2Q37_BLOCKS
 #define LBM_FLOAT_D2Q37_BLOCKS 3
 #endif
+#ifndef LBM_FLOAT_D3Q39_BLOCKS
+#define LBM_FLOAT_D3Q39_BLOCKS 3
+#endif
 template <class L, int P>
 constexpr int min_blocks() {
-  return P == P_FP64 ? 1 : (L::Q > 37 ? 2 : LBM_FLOAT_D2Q37_BLOCKS);
+  return P == P_FP64 ? 1 : (L::Q > 37 ? LBM_FLOAT_D3Q39_BLOCKS : LBM_FLOAT_D2Q37_BLOCKS);
 }
 
 // Line of the wall axis a block works on.  With walls, the six wall rows
