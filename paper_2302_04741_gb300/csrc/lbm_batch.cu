@@ -62,11 +62,20 @@ void drop_graph(lbm_batch* b) {
   }
 }
 
+// CTAs of a batch launch: LBM_BATCH_WAVES times the resident capacity, each
+// striding over the tiles.  Queued CTAs let the block scheduler start a new
+// CTA whenever one finishes, as in a plain launch: on GB300 16 waves gave the
+// ragged 64-grid mix 0.91 of the HBM roofline instead of 0.84 with one wave
+// (a strictly persistent grid), and 24 mixed D3Q39 boxes +4 %; 64 waves were
+// slower again.  A tuning hook (LBM_NVCC_DEFINES).
+#ifndef LBM_BATCH_WAVES
+#define LBM_BATCH_WAVES 16
+#endif
 int set_ctas(lbm_batch* b) {
   int bps = 0;
   BCUDA(b, b->ops->batch_occupancy(b->precision, b->force_order, b->spt, b->bx, &bps));
   if (bps < 1) return bfail(b, LBM_EINVAL, "batch kernel does not fit with block %d", b->bx);
-  b->ctas = bps * b->nsm;
+  b->ctas = bps * b->nsm * LBM_BATCH_WAVES;
   return LBM_OK;
 }
 

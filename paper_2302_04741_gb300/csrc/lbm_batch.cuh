@@ -7,8 +7,8 @@
 // run of blockDim.x * SPT consecutive sites of one grid's flattened index
 // (x fastest), so grids whose rows are shorter than a block keep every
 // thread busy; prefix[g] is the first global tile of grid g (prefix[ngrids]
-// = all tiles).  Persistent CTAs stride over the
-// global tiles, so grids of any mix of sizes share one launch, and every
+// = all tiles).  CTAs (several waves of the resident capacity) stride over
+// the global tiles, so grids of any mix of sizes share one launch, and every
 // site goes through exactly the device code of k_step (bit-identical
 // results to stepping each grid alone).
 #pragma once
