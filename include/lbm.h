@@ -257,11 +257,11 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * no-op. */
 void lbm_destroy(lbm_ctx *ctx);
 
-/* ---- Batches: many grids, one persistent launch per step. ----
+/* ---- Batches: many grids, one launch per step. ----
  *
  * Not in the paper (whose runs are single grids): independent simulations of
- * differing sizes and parameters are stepped together by one persistent
- * kernel that strides over the row tiles of all member grids, so small grids
+ * differing sizes and parameters are stepped together by one kernel whose
+ * blocks stride over the tiles of all member grids, so small grids
  * share the GPU instead of each paying a full launch.  Every site goes
  * through the same device code as lbm_step, so a grid's state after n batch
  * steps is bit-identical to n lbm_step calls on it alone.

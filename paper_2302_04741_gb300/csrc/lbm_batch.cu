@@ -1,4 +1,4 @@
-// lbm_batch.cu -- batches of contexts stepped by one persistent launch
+// lbm_batch.cu -- batches of contexts stepped by one launch per step
 // (lbm_batch_* in include/lbm.h), with CUDA-graph replay and an autotuner.
 #include <cuda_runtime.h>
 

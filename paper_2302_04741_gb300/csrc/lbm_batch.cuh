@@ -1,4 +1,4 @@
-// lbm_batch.cuh -- one persistent launch that steps a ragged set of grids.
+// lbm_batch.cuh -- one launch per step for a ragged set of grids.
 //
 // Every member grid keeps its own buffers and parameters; a device table
 // holds, per grid, its StepParams, both buffer pointers and the parity of the

@@ -4,7 +4,7 @@ Requests (independent simulations of differing sizes and force parameters)
 arrive over time.  A request is admitted as soon as a slot is free and the
 device has room for its populations (checked against free HBM); its context
 joins the running batch, so its steps overlap with every other resident
-simulation in the same persistent launches.  Each tick advances all resident
+simulation in the same batch launches.  Each tick advances all resident
 grids by min(tick_steps, smallest remaining step count) steps; requests that
 reach their step count are read out (physical moments), removed from the batch
 and freed, which frees their slot for the next arrival.
