@@ -134,31 +134,29 @@ struct F2 {
 __host__ __device__ constexpr F2 f2_of(double k) {
   return F2{float(k), float(k - double(float(k)))};
 }
-template <class R>
-__device__ __forceinline__ R kmul(double k, F2 k2, R x);
-template <>
-__device__ __forceinline__ float kmul<float>(double, F2 k2, float x) {
-  return fmaf(k2.hi, x, k2.lo * x);
+// EX = false (FP16 storage, whose rounding of ~5e-4 dwarfs the ~1e-8 a
+// float-rounded constant costs): one float multiply instead of two.
+template <class R, bool EX = true>
+__device__ __forceinline__ R kmul(double k, F2 k2, R x) {
+  if constexpr (sizeof(R) == sizeof(double)) return R(k) * x;
+  else if constexpr (EX) return fmaf(k2.hi, x, k2.lo * x);
+  else return k2.hi * x;
 }
-template <>
-__device__ __forceinline__ double kmul<double>(double k, F2, double x) {
-  return k * x;
-}
-template <class L, int I, class R>
+template <class L, int I, class R, bool EX = true>
 __device__ __forceinline__ R mul_w(R x) {
   constexpr double k = L::W(I);
   constexpr F2 k2 = f2_of(k);
-  return kmul<R>(k, k2, x);
+  return kmul<R, EX>(k, k2, x);
 }
-template <class L, class R>
+template <class L, class R, bool EX = true>
 __device__ __forceinline__ R mul_c(R x) {
   constexpr F2 k2 = f2_of(L::c);
-  return kmul<R>(L::c, k2, x);
+  return kmul<R, EX>(L::c, k2, x);
 }
-template <class L, class R>
+template <class L, class R, bool EX = true>
 __device__ __forceinline__ R mul_c2(R x) {
   constexpr F2 k2 = f2_of(L::c2);
-  return kmul<R>(L::c2, k2, x);
+  return kmul<R, EX>(L::c2, k2, x);
 }
 
 // e_i . v for compile-time e_i.

@@ -242,16 +242,17 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   using C = Codec<P>;
   using R = typename C::R;
   constexpr int NP = (L::Q - 1) / 2, NS = L::NSHELL, D = L::D;
+  constexpr bool EX = P != P_FP16S;  // quadrature constants as hi + lo pairs
   const size_t N = (size_t)p.N;
   const RawMoments<L, R> r = raw_moments<L, R>(d);
   // mid-point state (R1): rho, u = u~ + g/2, theta
   const R rho = R(1) + r.drho;
   const R irho = R(1) / rho;
   R u[3];
-  for (int a = 0; a < 3; ++a) u[a] = mul_c<L, R>(r.j[a] * irho) + R(0.5) * g[a];
+  for (int a = 0; a < 3; ++a) u[a] = mul_c<L, R, EX>(r.j[a] * irho) + R(0.5) * g[a];
   const R ut0 = u[0] - R(0.5) * g[0], ut1 = u[1] - R(0.5) * g[1], ut2 = u[2] - R(0.5) * g[2];
   const R g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-  const R Th = ((mul_c2<L, R>(r.k2) - R(D) * r.drho) * irho - (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)) *
+  const R Th = ((mul_c2<L, R, EX>(r.k2) - R(D) * r.drho) * irho - (ut0 * ut0 + ut1 * ut1 + ut2 * ut2)) *
                    R(1.0 / D) + g2 * R(0.25 / D);
   const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   const R gu = g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
@@ -263,8 +264,8 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   const R rkgu = FO >= 1 ? rho * kf * gu : R(0);
   R cu[3], cs[3];
   for (int a = 0; a < 3; ++a) {
-    cu[a] = mul_c<L, R>(u[a]);
-    cs[a] = mul_c<L, R>(rho * kf * g[a]);
+    cu[a] = mul_c<L, R, EX>(u[a]);
+    cs[a] = mul_c<L, R, EX>(rho * kf * g[a]);
   }
   // per-shell coefficients as polynomials in tx = Th |xi|^2 (constant hi + lo)
   //   A0 = a00 + tx (c1 + tx / 8 [NEQ 4]),  A1 = b0 + tx / 2,  A2 = g0 + tx / 4 [NEQ 4]
@@ -288,10 +289,10 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
     constexpr int sh = S;
     constexpr double X2d = L::c2 * double(L::E2(sh));
     constexpr F2 X2f = f2_of(X2d);
-    const R tx = kmul<R>(X2d, X2f, Th);
+    const R tx = kmul<R, EX>(X2d, X2f, Th);
     R A0, A2;
     if constexpr (L::NEQ >= 4) {
-      A0 = fma(R(0.125) * tx, tx, kmul<R>(X2d, X2f, c1) + a00);
+      A0 = fma(R(0.125) * tx, tx, kmul<R, EX>(X2d, X2f, c1) + a00);
       A2 = fma(R(0.25), tx, g0c);
     } else {
       A0 = fma(R(0.5), tx, a00);
@@ -314,7 +315,7 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   }
   // rest particle: t = s' = 0
   typename C::T* __restrict__ fo = fout + site;
-  fo[0] = C::template encode<L, 0>(fma(d[0], om1, mul_w<L, 0>(P0[0])), p);
+  fo[0] = C::template encode<L, 0>(fma(d[0], om1, mul_w<L, 0, R, EX>(P0[0])), p);
   static_for<0, NP>([&](auto K) {
     constexpr int ip = 2 * K + 1, im = ip + 1;
     constexpr int sh = L::SH(ip);
@@ -330,8 +331,8 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
       od_in = od_in + edot<L, ip>(cs);
     }
     if constexpr (FO == 3) od_in += stress_pair<L, ip, R>(st);
-    const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip>(ev_in));
-    const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip>(od_in));
+    const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip, R, EX>(ev_in));
+    const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip, R, EX>(od_in));
     fo[ip * N] = C::template encode<L, ip>(ev + od, p);
     fo[im * N] = C::template encode<L, im>(ev - od, p);
   });
