@@ -541,3 +541,37 @@ def test_float_storage_moments_match_fp64_sums(lat, shape, fo):
         np.testing.assert_allclose(x, y, rtol=1e-14, atol=1e-16, err_msg=name)
     dq = np.max(np.abs(ma[3] - mb[3]))
     assert dq < 1e-14 * max(np.max(np.abs(mb[3])), 1e-3), dq
+
+
+def _create(lat=0, nx=32, ny=16, nz=1, tau=0.8, **opt):
+    o = lbm.options(**{k: v for k, v in opt.items() if k in (
+        "precision", "force_order", "bc", "block_x", "graph_steps", "kernel", "tma_stages", "mu",
+        "include_sigma", "overlap_steps")})
+    return lbm.lbm_create(lat, nx, ny, nz, tau, None, o)
+
+
+@pytest.mark.parametrize("kw,why", [
+    (dict(nx=0), "empty grid"),
+    (dict(nz=2), "D2Q37 with nz > 1"),
+    (dict(lat=1, nx=2048, ny=2048, nz=1024), "N >= 2^31"),
+    (dict(tau=0.5), "tau-hat <= 1/2"),
+    (dict(tau=float("nan")), "tau-hat not finite"),
+    (dict(precision=3), "unknown precision"),
+    (dict(force_order=3), "force order > 2"),
+    (dict(bc=(0, 1, 0), ny=5), "walled axis below 6 sites"),
+    (dict(bc=(1, 0, 0)), "walls off the last axis"),
+    (dict(nx=2), "periodic axis below 3 sites"),
+    (dict(block_x=48), "block width not a multiple of 32"),
+    (dict(graph_steps=3), "odd graph length"),
+    (dict(kernel=9), "unknown kernel"),
+    (dict(mu=-1.0), "negative viscosity"),
+    (dict(overlap_steps=2), "bad overlap switch"),
+    (dict(tma_stages=1), "TMA ring depth"),
+])
+def test_create_rejects_invalid_arguments(kw, why):
+    """Every invalid argument is caught before any device memory is taken:
+    LBM_EINVAL with a message, and no context."""
+    with pytest.raises(lbm.LbmError) as ei:
+        _create(**kw)
+    assert ei.value.status == lbm.LBM_EINVAL, why
+    assert str(ei.value), why
