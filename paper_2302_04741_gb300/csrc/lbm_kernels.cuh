@@ -283,8 +283,9 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   const R base = om * r.drho - rkgu;
   // rho om multiplies every direction's equilibrium part at this site, so its
   // rounding would act as a common factor (a coherent momentum / energy error
-  // per step): carry it as rom + rom_lo, with the exact FMA residual.
-  const R rom_lo = fma(rho, om, -rom);
+  // per step): carry it as rom + rom_lo, with the exact FMA residual (in
+  // double the product's rounding is far below the tolerances: rom_lo = 0).
+  const R rom_lo = sizeof(R) == sizeof(double) ? R(0) : fma(rho, om, -rom);
   static_for<0, NS>([&](auto S) {
     constexpr int sh = S;
     constexpr double X2d = L::c2 * double(L::E2(sh));
