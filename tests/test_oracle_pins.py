@@ -608,3 +608,60 @@ def test_diffuse_wall_gives_parabola_plus_kinetic_slip():
         dudy_wall = g0 / nu * ny * c / 2
         ell.append(slip[bulk].mean() / dudy_wall / ((tau - 0.5) * c))
     assert all(0.5 < e < 2.0 for e in ell) and ell[1] > ell[0], ell
+
+
+@pytest.mark.parametrize("axis,bc", [(0, (0, 0, 0)), (1, (0, 1, 0)), (1, (0, 2, 0))])
+def test_mirror_symmetry(axis, bc):
+    """Reflecting the initial fields, the force and (for walls) the wall
+    temperatures across the grid's mid-plane reflects the result: the
+    lattice, the equilibrium, the force and the wall rules are all symmetric
+    under e_a -> -e_a.  Sums run in a different order, so the agreement is to
+    round-off, not bitwise."""
+    lat, nx, ny = oracle.D2Q37, 9, 8
+    N = nx * ny
+    g = 1e-3 * (W.uniform(4, 14, 2 * N).reshape(2, N) - 0.5)
+    rho, u, T = smooth_random_state(lat, (nx, ny, 1), 8)
+    T_lo, T_hi = (1.0, 1.04, 1.0), (1.0, 0.97, 1.0)
+
+    def flip(v, sign_comp=None):
+        v = np.array(v, dtype=np.float64).reshape(-1, ny, nx)
+        v = np.flip(v, axis=2 - axis).copy()
+        if sign_comp is not None:
+            v[sign_comp] *= -1
+        return v.reshape(-1, N).squeeze()
+
+    a = make_sim(lat, (nx, ny, 1), 0.75, g, bc=bc, T_lo=T_lo, T_hi=T_hi)
+    a.init(rho, u, T)
+    a.step(5)
+    b = make_sim(lat, (nx, ny, 1), 0.75, flip(g, axis), bc=bc,
+                 T_lo=T_hi if axis == 1 else T_lo, T_hi=T_lo if axis == 1 else T_hi)
+    b.init(flip(rho), flip(u, axis), flip(T))
+    b.step(5)
+    ra, ua, Ta, qa = a.moments()
+    rb, ub, Tb, qb = b.moments()
+    np.testing.assert_allclose(flip(ra), rb, rtol=1e-13)
+    np.testing.assert_allclose(flip(Ta), Tb, rtol=1e-13)
+    np.testing.assert_allclose(flip(ua, axis), ub, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(flip(qa, axis), qb, rtol=0, atol=1e-14)
+
+
+@pytest.mark.slow
+def test_sigma_bar_vanishes_in_static_conduction():
+    """In a fluid at rest -- here the steady conduction between thermal walls
+    -- the deviatoric stress vanishes (no velocity gradient), although the
+    temperature varies (Sec. 3.2 notes the same for the rotating cylinders):
+    no shear stress anywhere, and the normal-stress difference lives only in
+    the walls' kinetic layer, decaying ~e-fold per row into the bulk."""
+    lat, nx, ny, tau = oracle.D2Q37, 3, 24, 1.0
+    N = nx * ny
+    sim = make_sim(lat, (nx, ny, 1), tau, np.zeros((2, N)), bc=(0, 2, 0),
+                   T_lo=(1, 1.05, 1), T_hi=(1, 0.95, 1))
+    sim.init(np.ones(N), np.zeros((2, N)), np.ones(N))
+    sim.step(4000)
+    rho, u, T, q, sig = sim.moments(with_sigma=True)
+    s = sig.reshape(2, 2, ny, nx)[:, :, :, 0]
+    assert np.max(np.abs(s[0, 1])) < 1e-15
+    wall = abs(s[0, 0, 0])
+    assert wall > 1e-5
+    centre = np.max(np.abs(s[0, 0, ny // 2 - 2:ny // 2 + 2]))
+    assert centre < 1e-4 * wall, (centre, wall)
