@@ -323,7 +323,7 @@ void lbm_batch_destroy(lbm_batch *b);
  *        number of sites with a non-finite moment, rho <= 0 or T <= 0.
  *
  * Nothing is allocated: the per-block partial sums live in a static device
- * array of LBM_STATIC_MAX_TILES row tiles (128 sites along x each; 2.75 MB
+ * array of LBM_STATIC_MAX_TILES row tiles (128 sites along x each; 3.0 MB
  * held by every GPU that loads the library until the process exits).  Grids
  * needing more tiles, ceil(nx/128)*ny*nz > LBM_STATIC_MAX_TILES, are rejected
  * with LBM_EINVAL.  The first call on a device looks up the array's device

@@ -542,7 +542,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     const long long tiles = (long long)((nx + 127) / 128) * ny * nz;
     c->nblk_cons = (int)std::min<long long>(tiles, 4LL * (nsm > 0 ? nsm : 1));
   }
-  const size_t pb = sizeof(double) * 2 * lbm::NCONS * c->nblk_cons;
+  const size_t pb = sizeof(double) * lbm::CONS_SLOT * c->nblk_cons;
   if (cudaMalloc(&c->part, pb) != cudaSuccess || cudaMalloc(&c->bad, sizeof(unsigned) * c->nblk_cons) != cudaSuccess ||
       cudaMalloc(&c->dres, sizeof(double) * (2 * lbm::NCONS + 2)) != cudaSuccess ||
       cudaMalloc(&c->dmax, sizeof(unsigned)) != cudaSuccess ||
@@ -935,46 +935,3 @@ int ctx_fail(lbm_ctx* c, int code, const char* fmt, ...) {
 }
 }  // namespace lbm
 
-// ------------------------------------------------ final conservation pass
-namespace lbm {
-__global__ void __launch_bounds__(256) k_conserved_final(const double* __restrict__ part,
-                                                         const unsigned* __restrict__ badcount,
-                                                         int nblocks, double* __restrict__ out) {
-  __shared__ double sh_s[256][NCONS], sh_c[256][NCONS];
-  __shared__ unsigned sh_b[256];
-  KSum acc[NCONS];
-  for (int k = 0; k < NCONS; ++k) acc[k] = KSum{0.0, 0.0};
-  unsigned b = 0;
-  for (int blk = threadIdx.x; blk < nblocks; blk += 256) {
-    for (int k = 0; k < NCONS; ++k)
-      acc[k] = ksum_merge(acc[k], KSum{part[(size_t)blk * 2 * NCONS + 2 * k],
-                                       part[(size_t)blk * 2 * NCONS + 2 * k + 1]});
-    b += badcount[blk];
-  }
-  for (int k = 0; k < NCONS; ++k) {
-    sh_s[threadIdx.x][k] = acc[k].s;
-    sh_c[threadIdx.x][k] = acc[k].c;
-  }
-  sh_b[threadIdx.x] = b;
-  __syncthreads();
-  for (int half = 128; half > 0; half >>= 1) {
-    if (threadIdx.x < half) {
-      for (int k = 0; k < NCONS; ++k) {
-        KSum r = ksum_merge(KSum{sh_s[threadIdx.x][k], sh_c[threadIdx.x][k]},
-                            KSum{sh_s[threadIdx.x + half][k], sh_c[threadIdx.x + half][k]});
-        sh_s[threadIdx.x][k] = r.s;
-        sh_c[threadIdx.x][k] = r.c;
-      }
-      sh_b[threadIdx.x] += sh_b[threadIdx.x + half];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < NCONS; ++k) {
-      out[2 * k] = sh_s[0][k];
-      out[2 * k + 1] = sh_c[0][k];
-    }
-    out[2 * NCONS] = (double)sh_b[0];
-  }
-}
-}  // namespace lbm

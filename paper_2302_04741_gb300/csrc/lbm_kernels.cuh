@@ -717,24 +717,9 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
   for (int a = 0; a < D; ++a) q[a * N + site] = kq * (C3[a] + 0.5 * FC3[a]);
 }
 
-// ------------------------------------------------- conservation sums (FP64)
-// Compensated (Neumaier two-sum) accumulation: a value is the pair (s, c)
-// with the exact sum s + c up to the rounding of c.
-struct KSum {
-  double s, c;
-};
-__device__ __forceinline__ KSum ksum_add(KSum a, double v) {
-  const double t = a.s + v;
-  const double e = fabs(a.s) >= fabs(v) ? (a.s - t) + v : (v - t) + a.s;
-  return {t, a.c + e};
-}
-__device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
-  KSum r = ksum_add(a, b.s);
-  r.c += b.c;
-  return r;
-}
-
-// Compensated (Neumaier) running sum in the arithmetic type R of a kernel.
+// ------------------------------------------------------ conservation sums
+// Compensated (Neumaier) running sum in the arithmetic type R of a kernel:
+// the exact sum is s + c up to the rounding of c.
 template <class R>
 struct RSum {
   R s = R(0), c = R(0);
@@ -743,66 +728,146 @@ struct RSum {
     c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
     s = t;
   }
+  __device__ __forceinline__ void merge(const RSum& o) {
+    add(o.s);
+    c += o.c;
+  }
   __device__ __forceinline__ double value() const { return double(s) + double(c); }
 };
 
 // Quantities reduced: 0 mass, 1..3 momentum, 4 energy; plus a count of bad sites.
 constexpr int NCONS = 5;
+// Doubles per block in the partials array: the NCONS compensated pairs of the
+// block's per-site sums, stored in the kernel's type R from the start of the
+// slot, then the block's number of fluid sites (a double at index 2 NCONS).
+constexpr int CONS_SLOT = 2 * NCONS + 1;
 
-// Block sum of per-thread values (plain doubles) with compensated adds, in a
-// fixed order: the values go to shared memory, then 8 threads per quantity
-// each sum a contiguous run of BS / 8 values, and one thread per quantity
-// merges those 8 partial sums.  (A shuffle tree makes every thread do the
-// compensated merges of every level on the FP64 pipe, which dominated this
-// otherwise light pass.)  Writes the (s, c) pair of each quantity and the
-// bad-site count of block `block`.
-template <int BS>
-__device__ __forceinline__ void block_reduce_store(const double (&v)[NCONS], unsigned bad,
-                                                   double* __restrict__ part, unsigned* badcount,
-                                                   int block) {
+// Block-wide merge of per-thread compensated pairs in a fixed order: the
+// pairs go to shared memory, 8 threads per quantity merge contiguous runs of
+// BS / 8, thread 0 merges the 8 runs; the counts are summed by warp shuffles.
+// All in R: with float storage no FP64 instruction runs here (GB300 issues
+// FP64 at a small fraction of the FP32 rate, so a double-precision tree at
+// the end of every block was the tail of the pass).  The totals are valid in
+// thread 0 only.
+template <class R, int BS>
+__device__ __forceinline__ void reduce_block(const RSum<R> (&v)[NCONS], unsigned n, unsigned bad,
+                                             RSum<R> (&tot)[NCONS], unsigned& ntot,
+                                             unsigned& btot) {
   static_assert(BS % 32 == 0 && BS >= 64, "block size");
   constexpr int RUN = BS / 8;
-  __shared__ double sh_v[NCONS][BS];
-  __shared__ KSum sh_p[NCONS][8];
-  __shared__ unsigned sh_bad[BS / 32];
+  __shared__ R sh_s[NCONS][BS], sh_c[NCONS][BS];
+  __shared__ RSum<R> sh_p[NCONS][8];
+  __shared__ unsigned sh_n[BS / 32], sh_b[BS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k < NCONS; ++k) sh_v[k][tid] = v[k];
+  for (int k = 0; k < NCONS; ++k) {
+    sh_s[k][tid] = v[k].s;
+    sh_c[k][tid] = v[k].c;
+  }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, off);
-  if (lane == 0) sh_bad[warp] = bad;
+  for (int off = 16; off > 0; off >>= 1) {
+    n += __shfl_down_sync(0xffffffffu, n, off);
+    bad += __shfl_down_sync(0xffffffffu, bad, off);
+  }
+  if (lane == 0) {
+    sh_n[warp] = n;
+    sh_b[warp] = bad;
+  }
   __syncthreads();
   if (tid < NCONS * 8) {
     const int k = tid / 8, r = tid % 8;
-    KSum acc{0.0, 0.0};
-    for (int j = 0; j < RUN; ++j) acc = ksum_add(acc, sh_v[k][r * RUN + j]);
-    sh_p[k][r] = acc;
+    RSum<R> a{sh_s[k][r * RUN], sh_c[k][r * RUN]};
+    for (int j = 1; j < RUN; ++j) a.merge(RSum<R>{sh_s[k][r * RUN + j], sh_c[k][r * RUN + j]});
+    sh_p[k][r] = a;
   }
   __syncthreads();
-  if (tid < NCONS) {
-    KSum acc = sh_p[tid][0];
-    for (int r = 1; r < 8; ++r) acc = ksum_merge(acc, sh_p[tid][r]);
-    part[(size_t)block * 2 * NCONS + 2 * tid] = acc.s;
-    part[(size_t)block * 2 * NCONS + 2 * tid + 1] = acc.c;
-  }
   if (tid == 0) {
-    unsigned b2 = 0;
-    for (int w = 0; w < BS / 32; ++w) b2 += sh_bad[w];
-    badcount[block] = b2;
+    for (int k = 0; k < NCONS; ++k) {
+      RSum<R> a = sh_p[k][0];
+      for (int r = 1; r < 8; ++r) a.merge(sh_p[k][r]);
+      tot[k] = a;
+    }
+    ntot = 0u;
+    btot = 0u;
+    for (int w = 0; w < BS / 32; ++w) {
+      ntot += sh_n[w];
+      btot += sh_b[w];
+    }
+  }
+}
+
+// Mass, momentum and energy (as s, c pairs of doubles: out[2k], out[2k + 1])
+// from the grid's sums.  Uniform g: S = (sum drho, sum j, sum k2) and, with
+// n fluid sites, mass M = n + S0, momentum c J + M g / 2, energy
+// (D n + c^2 K2 + c J.g + M |g|^2 / 2) / 2 (mid-point values of R1).  Other
+// forces: S = (sum drho, sum of per-site momentum, sum of per-site energy
+// less D / 2), so the momentum is S1..3 and the energy D n / 2 + S4.
+template <class L, class R>
+__device__ __forceinline__ void conserved_from_sums(const RSum<R> (&S)[NCONS], double n,
+                                                    const StepParams& p, double* out) {
+  constexpr int D = L::D;
+  double v[NCONS];
+  for (int k = 0; k < NCONS; ++k) v[k] = S[k].value();
+  const double mass = n + v[0];
+  double res[NCONS];
+  res[0] = mass;
+  res[1] = res[2] = res[3] = 0.0;
+  if (p.gkind == G_UNIFORM) {
+    const double g[3] = {p.g0[0], p.g0[1], D == 3 ? p.g0[2] : 0.0};
+    double jg = 0.0;
+    for (int a = 0; a < D; ++a) {
+      res[1 + a] = L::c * v[1 + a] + 0.5 * g[a] * mass;
+      jg += L::c * v[1 + a] * g[a];
+    }
+    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    res[4] = 0.5 * (double(D) * n + L::c2 * v[4] + jg + 0.5 * g2 * mass);
+  } else {
+    for (int a = 0; a < D; ++a) res[1 + a] = v[1 + a];
+    res[4] = 0.5 * double(D) * n + v[4];
+  }
+  for (int k = 0; k < NCONS; ++k) {
+    out[2 * k] = res[k];
+    out[2 * k + 1] = 0.0;
+  }
+}
+
+// Merge of the partials of nblocks blocks (slot layout CONS_SLOT) by one
+// block of BS threads, in a fixed order: thread t takes blocks t, t + BS, ...
+// then the block merge above.  Thread 0 writes out[0 .. 2 NCONS - 1] (s, c
+// pairs) and out[2 NCONS] = the bad-site count.
+template <class L, class R, int BS>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
+                                                const unsigned* __restrict__ badcount, int nblocks,
+                                                const StepParams& p, double* out) {
+  RSum<R> f[NCONS];
+  unsigned n = 0u, b = 0u;
+  for (int blk = threadIdx.x; blk < nblocks; blk += BS) {
+    const double* slot = part + (size_t)blk * CONS_SLOT;
+    const R* rs = reinterpret_cast<const R*>(slot);
+    for (int k = 0; k < NCONS; ++k) f[k].merge(RSum<R>{__ldcg(rs + 2 * k), __ldcg(rs + 2 * k + 1)});
+    n += (unsigned)__ldcg(slot + 2 * NCONS);
+    b += __ldcg(badcount + blk);
+  }
+  RSum<R> tot[NCONS];
+  unsigned ntot, btot;
+  reduce_block<R, BS>(f, n, b, tot, ntot, btot);
+  if (threadIdx.x == 0) {
+    conserved_from_sums<L, R>(tot, double(ntot), p, out);
+    out[2 * NCONS] = double(btot);
   }
 }
 
 // Grid-stride pass: block b handles row tiles b, b + gridDim.x, ... (one
-// site per thread and tile; threads past the row end contribute zeros).  Per
-// site only the raw moments are needed, in the codec's arithmetic precision:
-// mass rho = 1 + drho, momentum rho u = c j + rho g / 2, energy
+// site per thread and tile; threads past the row end contribute nothing).
+// Per site only the raw moments are needed, in the codec's arithmetic
+// precision: mass rho = 1 + drho, momentum rho u = c j + rho g / 2, energy
 // rho (|u|^2 + D theta) / 2 = (K + c j.g + rho |g|^2 / 2) / 2 with
 // K = D + c^2 k2 (mid-point values of R1, no division).  With a uniform g
-// these are linear in the per-site sums of drho, j and k2, so a thread sums
-// only those (in double) and forms its momentum and energy once; otherwise
-// it sums the per-site values.  The block and final merges are compensated
-// (two-sum).  The number of blocks is fixed by the caller, so the summation
-// order, and the result, are deterministic for a grid.  part:
-// gridDim.x * 2 * NCONS doubles, badcount: gridDim.x.
+// these are linear in the sums of drho, j and k2, so a thread sums only
+// those; otherwise it sums the per-site momentum and energy.  Each thread
+// keeps compensated pairs in R; the block merges them (reduce_block) and
+// writes its slot of `part` (CONS_SLOT doubles per block) and its bad-site
+// count.  The number of blocks is fixed by the caller, so the summation
+// order, and the result, are deterministic for a grid.
 //
 // ticket != nullptr: the last block to finish (by an atomic ticket) also
 // reduces all partials in block order into out (the k_conserved_final
@@ -826,66 +891,69 @@ __global__ void __launch_bounds__(128, LBM_CONSERVED_BLOCKS) k_conserved(const t
   const int ntx = (p.nx + 127) / 128;
   const int ntiles = ntx * p.ny * p.nz;
   const bool uniform = p.gkind == G_UNIFORM;
-  double acc[NCONS] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  // uniform force: per-thread compensated sums in the codec's precision (no
-  // FP64 work per site)
-  RSum<R> sdrho{}, sj[3] = {}, sk2{};
-  int count = 0;
-  unsigned bad = 0;
+  RSum<R> sums[NCONS];
+  unsigned count = 0u, bad = 0u;
+  const bool walls = p.wall != W_NONE;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // the wall rows, whose pull also gathers the wall sums, come first so
+    // that they do not form the tail of the pass
     const int xt = t % ntx, row = t / ntx;
-    const int y = row % p.ny, z = row / p.ny;
+    const int y = D == 2 ? wall_rows_first(row, p.ny, walls) : row % p.ny;
+    const int z = D == 3 ? wall_rows_first(row / p.ny, p.nz, walls) : 0;
     const int x = xt * 128 + threadIdx.x;
     if (x >= p.nx) continue;
     const int site = (z * p.ny + y) * p.nx + x;
     if (p.solid && p.solid[site]) continue;
     R d[Q];
+    const int a = D == 2 ? y : z;
+    const int nA = D == 2 ? p.ny : p.nz;
+    const int wx0 = xt * 128 + (threadIdx.x & ~31);
+    const bool interior = !(walls && (a < 3 || a >= nA - 3)) && wx0 >= 3 && wx0 + 31 <= p.nx - 4;
     if (p.solid) pull_solid<L, P, R>(fin, p, x, y, z, site, d);
+    else if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
     else pull<L, P, R>(fin, p, x, y, z, d);
     R g[3];
     site_force_r<D, R>(p, x, y, z, site, g);
     const RawMoments<L, R> r = raw_moments<L, R>(d);
-    if (uniform) {
-      ++count;
-      sdrho.add(r.drho);
-      for (int a = 0; a < D; ++a) sj[a].add(r.j[a]);
-      sk2.add(r.k2);
-    } else {
-      const double rho = 1.0 + double(r.drho);
-      double jc[3], jg = 0.0, g2 = 0.0;
-      for (int a = 0; a < 3; ++a) {
-        jc[a] = L::c * double(r.j[a]);
-        jg += jc[a] * double(g[a]);
-        g2 += double(g[a]) * double(g[a]);
-      }
-      acc[0] += rho;
-      for (int a = 0; a < D; ++a) acc[1 + a] += jc[a] + 0.5 * rho * double(g[a]);
-      acc[4] += 0.5 * (double(D) + L::c2 * double(r.k2) + jg + 0.5 * rho * g2);
-    }
-    // positivity check in the codec's precision:
-    // D theta = (K - |c j|^2 / rho) / rho + g^2 / 4, K = D + c^2 k2
-    const R rr = R(1) + r.drho;
-    const R K = R(D) + mul_c2<L, R>(r.k2);
+    ++count;
+    sums[0].add(r.drho);
     const R j0 = mul_c<L, R>(r.j[0]), j1 = mul_c<L, R>(r.j[1]), j2 = mul_c<L, R>(r.j[2]);
-    const R th = ((K - (j0 * j0 + j1 * j1 + j2 * j2) / rr) / rr +
-                  R(0.25) * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2])) * R(1.0 / D);
-    const bool finite = isfinite(rr) && isfinite(K) && isfinite(th);
-    bad += (!finite || !(rr > R(0)) || !(th > R(0))) ? 1u : 0u;
-  }
-  if (uniform) {
-    const double g[3] = {p.g0[0], p.g0[1], D == 3 ? p.g0[2] : 0.0};
-    double J[3] = {0.0, 0.0, 0.0}, jg = 0.0;
-    for (int a = 0; a < D; ++a) {
-      J[a] = sj[a].value();
-      jg += L::c * J[a] * g[a];
+    const R rr = R(1) + r.drho;
+    const R g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    if (uniform) {
+      for (int a2 = 0; a2 < D; ++a2) sums[1 + a2].add(r.j[a2]);
+      sums[4].add(r.k2);
+    } else {
+      const R hr = R(0.5) * rr;
+      sums[1].add(fma(hr, g[0], j0));
+      sums[2].add(fma(hr, g[1], j1));
+      if (D == 3) sums[3].add(fma(hr, g[2], j2));
+      const R jg = j0 * g[0] + j1 * g[1] + j2 * g[2];
+      sums[4].add(R(0.5) * (mul_c2<L, R>(r.k2) + jg + R(0.5) * rr * g2));
     }
-    const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    const double mass = double(count) + sdrho.value();  // sum of rho = 1 + drho
-    acc[0] = mass;
-    for (int a = 0; a < D; ++a) acc[1 + a] = L::c * J[a] + 0.5 * g[a] * mass;
-    acc[4] = 0.5 * (double(D) * count + L::c2 * sk2.value() + jg + 0.5 * g2 * mass);
+    // positivity check in the codec's precision, without divisions:
+    // D theta = (K - |c j|^2 / rho) / rho + g^2 / 4 with K = D + c^2 k2, so
+    // for rho > 0, theta > 0 exactly when e = K rho - |c j|^2 + rho^2 g^2 / 4
+    // > 0; a NaN or infinite moment makes e NaN or infinite
+    const R K = R(D) + mul_c2<L, R>(r.k2);
+    const R e = fma(rr * rr, R(0.25) * g2, fma(K, rr, -(j0 * j0 + j1 * j1 + j2 * j2)));
+    bad += (rr > R(0) && e > R(0) && isfinite(e)) ? 0u : 1u;
   }
-  block_reduce_store<128>(acc, bad, part, badcount, blockIdx.x);
+  {
+    RSum<R> tot[NCONS];
+    unsigned ntot, btot;
+    reduce_block<R, 128>(sums, count, bad, tot, ntot, btot);
+    if (threadIdx.x == 0) {
+      double* slot = part + (size_t)blockIdx.x * CONS_SLOT;
+      R* rs = reinterpret_cast<R*>(slot);
+      for (int k = 0; k < NCONS; ++k) {
+        rs[2 * k] = tot[k].s;
+        rs[2 * k + 1] = tot[k].c;
+      }
+      slot[2 * NCONS] = double(ntot);
+      badcount[blockIdx.x] = btot;
+    }
+  }
   if (!ticket) return;
   // the last block to finish reduces every block's partials, in block order
   __shared__ bool last;
@@ -896,47 +964,23 @@ __global__ void __launch_bounds__(128, LBM_CONSERVED_BLOCKS) k_conserved(const t
   __syncthreads();
   if (!last) return;
   __threadfence();
-  __shared__ KSum fk[NCONS][128];
-  __shared__ unsigned fbs[128];
-  for (int k = 0; k < NCONS; ++k) {
-    KSum f{0.0, 0.0};
-    for (int blk = threadIdx.x; blk < (int)gridDim.x; blk += 128)
-      f = ksum_merge(f, KSum{__ldcg(part + (size_t)blk * 2 * NCONS + 2 * k),
-                             __ldcg(part + (size_t)blk * 2 * NCONS + 2 * k + 1)});
-    fk[k][threadIdx.x] = f;
-  }
-  unsigned fb = 0;
-  for (int blk = threadIdx.x; blk < (int)gridDim.x; blk += 128) fb += __ldcg(badcount + blk);
-  fbs[threadIdx.x] = fb;
-  __syncthreads();
-  __shared__ KSum fr[NCONS][8];
-  if (threadIdx.x < NCONS * 8) {  // 8 runs of 16 per quantity, then the runs
-    const int k = threadIdx.x / 8, r = threadIdx.x % 8;
-    KSum f = fk[k][r * 16];
-    for (int j = 1; j < 16; ++j) f = ksum_merge(f, fk[k][r * 16 + j]);
-    fr[k][r] = f;
-  }
-  __syncthreads();
-  if (threadIdx.x < NCONS) {
-    KSum f = fr[threadIdx.x][0];
-    for (int r = 1; r < 8; ++r) f = ksum_merge(f, fr[threadIdx.x][r]);
-    out[2 * threadIdx.x] = f.s;
-    out[2 * threadIdx.x + 1] = f.c;
-  }
+  reduce_partials<L, R, 128>(part, badcount, gridDim.x, p, out);
   if (threadIdx.x == 0) {
-    unsigned b2 = 0;
-    for (int j = 0; j < 128; ++j) b2 += fbs[j];
-    out[2 * NCONS] = double(b2);
     out[2 * NCONS + 1] = err ? double(*(volatile const int*)err) : 0.0;
     *ticket = 0u;
   }
 }
 
-// Final pass: one block of 256 threads reduces the partials in a fixed order.
-// out: 2 * NCONS doubles (s, c pairs) followed by the bad-site count (as double).
-__global__ void __launch_bounds__(256) k_conserved_final(const double* __restrict__ part,
+// Final pass of the two-kernel form: one block of 128 threads merges the
+// partials of k_conserved (launched without a ticket) into out: 2 NCONS
+// doubles (s, c pairs) followed by the bad-site count (as double).
+template <class L, int P>
+__global__ void __launch_bounds__(128) k_conserved_final(const double* __restrict__ part,
                                                          const unsigned* __restrict__ badcount,
-                                                         int nblocks, double* __restrict__ out);
+                                                         int nblocks, double* __restrict__ out,
+                                                         const StepParams p) {
+  reduce_partials<L, typename Codec<P>::R, 128>(part, badcount, nblocks, p, out);
+}
 
 // ------------------------------------------------------ state access
 template <class L, int P>

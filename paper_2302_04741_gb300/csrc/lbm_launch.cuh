@@ -24,6 +24,9 @@ struct LatticeOps {
   cudaError_t (*conserved)(int P, const void* fin, double* part, unsigned* bad,
                            unsigned* ticket, double* out, const int* err,
                            const StepParams& p, int nblocks, cudaStream_t s);
+  // two-kernel form: merge the partials of a ticketless conserved() into out
+  cudaError_t (*conserved_final)(int P, const double* part, const unsigned* bad, int nblocks,
+                                 double* out, const StepParams& p, cudaStream_t s);
   cudaError_t (*pulled)(int P, const void* fin, double* out, const StepParams& p, cudaStream_t s);
   cudaError_t (*state)(int P, int dir, void* f, double* io, const StepParams& p, cudaStream_t s);
   // TMA-staged step (FP32-shifted and FP16-scaled storage only)
@@ -134,6 +137,14 @@ struct Ops {
       k_conserved<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, part, bad, ticket, out, err, p);
     else
       k_conserved<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, part, bad, ticket, out, err, p);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t conserved_final(int P, const double* part, const unsigned* bad, int nblocks,
+                                     double* out, const StepParams& p, cudaStream_t s) {
+    if (P == P_FP64) k_conserved_final<L, P_FP64><<<1, 128, 0, s>>>(part, bad, nblocks, out, p);
+    else if (P == P_FP32S) k_conserved_final<L, P_FP32S><<<1, 128, 0, s>>>(part, bad, nblocks, out, p);
+    else k_conserved_final<L, P_FP16S><<<1, 128, 0, s>>>(part, bad, nblocks, out, p);
     return cudaGetLastError();
   }
 
@@ -277,7 +288,7 @@ struct Ops {
   }
 
   static LatticeOps table() {
-    return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &pulled, &state,
+    return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &conserved_final, &pulled, &state,
                       &tma_smem, &tma_prepare, &step_tma, &async_occupancy, &step_async,
                       &batch_occupancy, &batch_step, &wave_occupancy, &step_wave};
   }

@@ -10,7 +10,7 @@
 // the raw state and writes the sums to memory the caller already owns.
 //
 // Its per-block partial sums live in the file-scope static device arrays
-// below, a fixed 2.75 MB on every GPU that loads the library, held until the
+// below, a fixed 3.0 MB on every GPU that loads the library, held until the
 // process exits.  Host code cannot use the array names as addresses (they
 // name host-side shadows), so the address is looked up once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
@@ -29,7 +29,7 @@ namespace {
 constexpr int kMaxTiles = LBM_STATIC_MAX_TILES;  // row tiles of 128 sites along x
 constexpr int kMaxDevices = 64;
 
-static __device__ __align__(256) double s_part[kMaxTiles * 2 * lbm::NCONS];
+static __device__ __align__(256) double s_part[kMaxTiles * lbm::CONS_SLOT];
 static __device__ __align__(256) unsigned s_bad[kMaxTiles];
 static __device__ __align__(256) double s_res[2 * lbm::NCONS + 1];
 
@@ -186,8 +186,7 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, nullptr, nullptr, nullptr, p,
                                  nblocks, st);
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "conservation kernel launch failed", e);
-  lbm::k_conserved_final<<<1, 256, 0, st>>>(s->part, s->bad, nblocks, s->res);
-  e = cudaGetLastError();
+  e = ops->conserved_final(o.precision, s->part, s->bad, nblocks, s->res, p, st);
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "final reduction launch failed", e);
   k_static_combine<<<1, 32, 0, st>>>(s->res, out);
   e = cudaGetLastError();
