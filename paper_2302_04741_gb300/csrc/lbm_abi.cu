@@ -489,6 +489,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   if (p.mu == 0.0) p.mu_f = 0.0f;
   for (int a = 0; a < 3; ++a) p.g0_f[a] = (float)p.g0[a];
   p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
+  p.l2_evict_first = lbm::l2_evict_first_for(2 * fbytes, c->device);
   if (wall != lbm::W_NONE) {
     if (lat == LBM_D2Q37) wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
     else wall_tables<lbm::D3Q39>(p, o.T_lo[D - 1], o.T_hi[D - 1]);

@@ -85,10 +85,15 @@ int upload(lbm_batch* b) {
   const int TW = b->bx * b->spt;
   long long tiles = 0;
   const int n = (int)b->members.size();
+  size_t bytes = 0;  // the launch's working set: both buffers of every member
+  for (int g = 0; g < n; ++g)
+    bytes += 2 * (size_t)b->members[g]->Q * b->members[g]->N * b->members[g]->elem;
+  const int evict_first = lbm::l2_evict_first_for(bytes, b->device);
   for (int g = 0; g < n; ++g) {
     lbm_ctx* c = b->members[g];
     lbm::BatchGrid& G = b->h_grids[g];
     G.p = c->p;
+    G.p.l2_evict_first = evict_first;
     G.f[0] = c->f[0];
     G.f[1] = c->f[1];
     G.cur = c->cur;

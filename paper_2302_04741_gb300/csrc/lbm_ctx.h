@@ -12,6 +12,20 @@
 
 struct lbm_batch;
 
+namespace lbm {
+// Whether population loads should be evict-first in L2 (ld_pop_policy): the
+// working set of a step, `bytes` (both population buffers of every grid the
+// launch steps), is below 1.5 times the device's L2 size.
+inline int l2_evict_first_for(size_t bytes, int device) {
+  int l2 = 0;
+  if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device) != cudaSuccess || l2 <= 0) {
+    cudaGetLastError();
+    return 0;
+  }
+  return bytes <= (size_t)l2 * 3 / 2 ? 1 : 0;
+}
+}  // namespace lbm
+
 struct lbm_ctx {
   int lat = 0, D = 0, Q = 0, nx = 0, ny = 0, nz = 0;
   int N = 0;
@@ -29,7 +43,7 @@ struct lbm_ctx {
   unsigned char* solid = nullptr;  // solid-site flags (lbm_set_solid), N bytes
   double* wall_th = nullptr;   // wall temperature - 1 per site, N doubles
   float* wall_th_f = nullptr;  // its float copy
-  double* part = nullptr;      // conservation partials (2 * NCONS per block)
+  double* part = nullptr;      // conservation partials (CONS_SLOT doubles per block)
   unsigned* bad = nullptr;     // bad-site counts per block
   double* dres = nullptr;      // final reduction result (when hres is not mapped)
   unsigned* ticket = nullptr;  // last-block ticket of the conservation pass

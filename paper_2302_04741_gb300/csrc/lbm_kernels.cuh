@@ -63,7 +63,7 @@ __device__ __forceinline__ void site_force_r(const StepParams& p, int x, int y, 
 
 // Pull of all Q populations of site (x, y, z) with the boundary rules, decoded
 // to deviations in type RR.  The wall axis is the last axis (y in 2-D, z in 3-D).
-template <class L, int P, class RR, bool CG = false>
+template <class L, int P, class RR, int LD = LD_HINT>
 __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fin,
                                      const StepParams& p, int x, int y, int z, RR (&d)[L::Q]) {
   using C = Codec<P>;
@@ -85,7 +85,7 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
       constexpr int i = I;
       constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
       const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
-      d[i] = RR(C::template decode<L, i>(ldpop<C, CG>(fin + i * N + off), p));
+      d[i] = RR(C::template decode<L, i>(ldpop<C, LD>(fin + i * N + off, p), p));
     });
     return;
   }
@@ -105,7 +105,7 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
         if constexpr (eA != 0) {
           const bool leaves = side == 0 ? (eA < 0 && r + eA < 0) : (eA > 0 && r - eA < 0);
           if (leaves)
-            sum += RR(C::template decode<L, j>(ldpop<C, CG>(fin + j * N + colbase + row * lineA), p));
+            sum += RR(C::template decode<L, j>(ldpop<C, LD>(fin + j * N + colbase + row * lineA, p), p));
         }
       });
     }
@@ -118,11 +118,11 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
     const int sA = a - eA;
     if (sA >= 0 && sA < nA) {
       const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
-      d[i] = RR(C::template decode<L, i>(ldpop<C, CG>(fin + i * N + off), p));
+      d[i] = RR(C::template decode<L, i>(ldpop<C, LD>(fin + i * N + off, p), p));
     } else if (p.wall == W_BOUNCE) {
       constexpr int io = opposite<i>();
       const int mA = side == 0 ? eA - 1 - a : 2 * nA - 1 - sA;
-      d[i] = RR(C::template decode<L, io>(ldpop<C, CG>(fin + io * N + colbase + mA * lineA), p));
+      d[i] = RR(C::template decode<L, io>(ldpop<C, LD>(fin + io * N + colbase + mA * lineA, p), p));
     } else {
       d[i] = fma(rm1, RR(p.fw[side][i]), RR(p.fwd[side][i]));
     }
@@ -177,12 +177,12 @@ __device__ __forceinline__ void pull_solid(const typename Codec<P>::T* __restric
       constexpr int io = opposite<i>();
       constexpr RR w = RR(L::W(i));
       const RR a0 = wall_a0<L, i, RR>(ParamsOf<RR>::wall_th(p, src));
-      num += RR(C::template decode<L, io>(C::load(fin + io * N + site), p)) - w * a0;
+      num += RR(C::template decode<L, io>(C::load(fin + io * N + site, p), p)) - w * a0;
       den = fma(w, RR(1) + a0, den);
       walls |= 1ull << i;
       d[i] = a0;  // kept for the second pass
     } else {
-      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + src), p));
+      d[i] = RR(C::template decode<L, i>(C::load(fin + i * N + src, p), p));
     }
   });
   if (!walls) return;
@@ -197,7 +197,7 @@ __device__ __forceinline__ void pull_solid(const typename Codec<P>::T* __restric
 // source offset relative to the thread's own site, i*N + (row / plane shift)
 // - e_ix, is the same for the whole block (rows wrap only through the block's
 // y, z), so addresses are a per-thread base plus block-uniform offsets.
-template <class L, int P, class RR, bool CG = false>
+template <class L, int P, class RR, int LD = LD_HINT>
 __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __restrict__ fsite,
                                               const StepParams& p, int y, int z,
                                               RR (&d)[L::Q]) {
@@ -214,7 +214,7 @@ __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __rest
     constexpr int i = I;
     constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
     const long long off = i * N + dz[ez + 3] + dy[ey + 3] - ex;
-    d[i] = RR(C::template decode<L, i>(ldpop<C, CG>(fsite + off), p));
+    d[i] = RR(C::template decode<L, i>(ldpop<C, LD>(fsite + off, p), p));
   });
 }
 

@@ -141,7 +141,7 @@ __device__ __forceinline__ void pull_staged(const unsigned char* stage,
         if constexpr (eA != 0) {
           const bool leaves = side == 0 ? (eA < 0 && r + eA < 0) : (eA > 0 && r - eA < 0);
           if (leaves)
-            sum += R(C::template decode<L, j>(C::load(fin + j * N + colbase + row * lineA), p));
+            sum += R(C::template decode<L, j>(C::load(fin + j * N + colbase + row * lineA, p), p));
         }
       });
     }
@@ -160,12 +160,12 @@ __device__ __forceinline__ void pull_staged(const unsigned char* stage,
         const int sx = wrap3(xs, nx);
         const int sy = wrap3(y - ey, ny);
         const int sz = D == 3 ? wrap3(z - ez, nz) : 0;
-        d[i] = R(C::template decode<L, i>(C::load(fin + i * N + (sz * ny + sy) * nx + sx), p));
+        d[i] = R(C::template decode<L, i>(C::load(fin + i * N + (sz * ny + sy) * nx + sx, p), p));
       }
     } else if (p.wall == W_BOUNCE) {
       constexpr int io = opposite<i>();
       const int mA = side == 0 ? eA - 1 - a : 2 * nA - 1 - sA;
-      d[i] = R(C::template decode<L, io>(C::load(fin + io * N + colbase + mA * lineA), p));
+      d[i] = R(C::template decode<L, io>(C::load(fin + io * N + colbase + mA * lineA, p), p));
     } else {
       d[i] = fma(rm1, R(p.fw[side][i]), R(p.fwd[side][i]));
     }

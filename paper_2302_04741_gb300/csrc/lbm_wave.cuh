@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(WAVE_BX, wave_min_blocks<L, P>())
       R g[3];
       site_force_r<D, R>(p, x, y, z, site, g);
       R d[L::Q];
-      if (interior) pull_interior<L, P, R, true>(fin + site, p, y, z, d);
-      else pull<L, P, R, true>(fin, p, x, y, z, d);
+      if (interior) pull_interior<L, P, R, LD_CG>(fin + site, p, y, z, d);
+      else pull<L, P, R, LD_CG>(fin, p, x, y, z, d);
       collide_store<L, P, FO>(d, g, site, fout, p);
     }
     __threadfence();
