@@ -541,7 +541,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     const long long tiles = (long long)((nx + 127) / 128) * ny * nz;
-    c->nblk_cons = (int)std::min<long long>(tiles, 4LL * (nsm > 0 ? nsm : 1));
+    c->nblk_cons = (int)std::min<long long>(tiles, (long long)LBM_CONSERVED_BLOCKS * (nsm > 0 ? nsm : 1));
   }
   const size_t pb = sizeof(double) * lbm::CONS_SLOT * c->nblk_cons;
   if (cudaMalloc(&c->part, pb) != cudaSuccess || cudaMalloc(&c->bad, sizeof(unsigned) * c->nblk_cons) != cudaSuccess ||

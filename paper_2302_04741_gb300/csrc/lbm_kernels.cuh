@@ -874,7 +874,7 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
 // layout, plus out[2 NCONS + 1] = *err, the bounded-wait error flag) and
 // resets the ticket; out may be mapped host memory.
 // Resident 128-thread blocks per SM the conservation pass is compiled for
-// (its grid is 4 blocks per SM; LBM_CONSERVED_BLOCKS is a tuning hook).
+// (its grid is LBM_CONSERVED_BLOCKS blocks per SM, a tuning hook).
 #ifndef LBM_CONSERVED_BLOCKS
 #define LBM_CONSERVED_BLOCKS 4
 #endif

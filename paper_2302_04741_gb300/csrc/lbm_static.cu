@@ -182,7 +182,8 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   // the grid-stride pass writes one partial per block: at most one per tile
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_of_current());
-  const int nblocks = (int)(tiles < 4LL * nsm ? tiles : 4LL * nsm);
+  const long long cap = (long long)LBM_CONSERVED_BLOCKS * nsm;
+  const int nblocks = (int)(tiles < cap ? tiles : cap);
   cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, nullptr, nullptr, nullptr, p,
                                  nblocks, st);
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "conservation kernel launch failed", e);
