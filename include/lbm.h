@@ -212,10 +212,13 @@ int lbm_step(lbm_ctx *ctx, int n);
  * device buffer.  Synchronises the stream. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *q);
 
-/* Global sums over the grid, in double with compensated (two-sum) block
- * reductions in a fixed order (deterministic for a fixed grid): mass =
+/* Global sums over the grid (deterministic for a fixed grid): mass =
  * sum rho, mom[D] = sum rho u, energy = sum rho (|u|^2 + D theta)/2, all
- * physical mid-point values.  Any output may be NULL (host pointers).
+ * physical mid-point values.  Per-site moments and the compensated
+ * (two-sum) per-thread, block and grid merges run in the storage's
+ * arithmetic precision (double for LBM_FP64, float pairs otherwise, about
+ * 48 bits), in a fixed order; the totals are combined in double.  Any output
+ * may be NULL (host pointers).
  * Returns LBM_EUNSTABLE if any site has a non-finite moment, rho <= 0 or
  * theta <= 0 (the sums are still written).  Synchronises the stream. */
 int lbm_conserved(lbm_ctx *ctx, double *mass, double *mom, double *energy);
