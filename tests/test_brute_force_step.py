@@ -1,0 +1,177 @@
+"""Brute-force pin of one oracle step on tiny grids.
+
+The update of Eq. lbm is recomputed here in numpy from the definitions, by a
+route that shares nothing with the oracle's tensor code:
+
+* the Hermite equilibrium in product form.  A Maxwellian factorises over the
+  axes, so its Hermite coefficients are products of 1-D ones; for X normal
+  with mean u and variance theta the generating function
+  E[exp(X t - t^2/2)] = exp(u t + (theta - 1) t^2 / 2) gives
+  E[He_n(X)] = sum_k n! / (k! (n - 2k)! 2^k) (theta - 1)^k u^(n - 2k),
+  and f0_i = w_i rho sum_{|m| <= N_eq} prod_a E[He_{m_a}] He_{m_a}(xi_ia) / m_a!;
+* the force F = -g . grad_xi f_N of Eq. F by an index shift (Rodrigues):
+  -d/dxi_a [omega He_m] = omega He_{m + e_a}, so
+  F_i = w_i rho sum_a g_a sum_{|m| <= N} prod_b E[He_{m_b}] / m_b! He_{m + e_a}(xi_i);
+* the mid-point state of Sec. 2 (u = j / rho + g / 2, theta with the g^2 / 4D
+  term) and the pull with the wall rules written as loops over sites and
+  directions: half-way bounce-back in the same column, and the diffuse
+  thermal wall that re-emits, per column, the mass leaving through the wall
+  as a wall Maxwellian.
+
+Everything is FP64 on both sides; only the summation order differs.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2302_04741_gb300 import workloads as W
+
+from numpy.polynomial import hermite_e as He
+
+
+def he(n, x):
+    """Probabilists' Hermite polynomial He_n at x (numpy's coefficients)."""
+    c = np.zeros(n + 1)
+    c[n] = 1.0
+    return He.hermeval(x, c)
+
+
+def he_mean(n, u, theta):
+    """E[He_n(X)] for X normal with mean u and variance theta."""
+    return sum(math.factorial(n) / (math.factorial(k) * math.factorial(n - 2 * k) * 2 ** k)
+               * (theta - 1.0) ** k * u ** (n - 2 * k) for k in range(n // 2 + 1))
+
+
+def multi_indices(D, nmax):
+    return [m for m in itertools.product(range(nmax + 1), repeat=D) if sum(m) <= nmax]
+
+
+def feq_product(xi, w, rho, u, theta, neq):
+    D = xi.shape[1]
+    out = np.zeros(len(w))
+    for m in multi_indices(D, neq):
+        coef = rho * np.prod([he_mean(m[a], u[a], theta) / math.factorial(m[a]) for a in range(D)])
+        out += coef * np.prod([he(m[a], xi[:, a]) for a in range(D)], axis=0)
+    return w * out
+
+
+def force_shift(xi, w, rho, u, theta, g, order):
+    D = xi.shape[1]
+    out = np.zeros(len(w))
+    for m in multi_indices(D, order):
+        coef = rho * np.prod([he_mean(m[b], u[b], theta) / math.factorial(m[b]) for b in range(D)])
+        for a in range(D):
+            mm = list(m)
+            mm[a] += 1
+            out += g[a] * coef * np.prod([he(mm[b], xi[:, b]) for b in range(D)], axis=0)
+    return w * out
+
+
+def brute_step(fstar, lat, shape, tau, g, order, bc_wall=0, T_lo=1.0, T_hi=1.0):
+    """One step of Eq. lbm from the post-collision state fstar (Q, N).
+    bc_wall: 0 periodic, 1 bounce-back, 2 thermal wall on the last axis."""
+    D, Q, c, e, w, neq = oracle.lattice_info(lat)
+    e = e[:, :D]
+    xi = c * e.astype(float)
+    n = list(shape[:D])
+    A = D - 1                                     # wall axis
+    opp = [int(np.flatnonzero((e == -e[i]).all(axis=1))[0]) for i in range(Q)]
+    strides = [1, shape[0], shape[0] * shape[1]][:D]
+
+    def site(x):
+        return sum(x[a] * strides[a] for a in range(D))
+
+    # wall densities per column (thermal wall): emitted mass / emitted shape
+    rho_w = {}
+    if bc_wall == 2:
+        for side, Tw in ((0, T_lo), (1, T_hi)):
+            f0w = feq_product(xi, w, 1.0, np.zeros(D), Tw, neq)
+            den = sum((e[i, A] if side == 0 else -e[i, A]) * f0w[i]
+                      for i in range(Q) if (e[i, A] > 0 if side == 0 else e[i, A] < 0))
+            for col in itertools.product(*[range(n[a]) for a in range(A)]):
+                leave = 0.0
+                for r in range(3):
+                    row = r if side == 0 else n[A] - 1 - r
+                    for j in range(Q):
+                        dest = row + e[j, A]
+                        if (side == 0 and dest < 0) or (side == 1 and dest >= n[A]):
+                            leave += fstar[j, site(list(col) + [row])]
+                rho_w[(side, col)] = (leave / den, f0w)
+    N = fstar.shape[1]
+    out = np.zeros_like(fstar)
+    gg = np.asarray(g).reshape(D, N)
+    for x in itertools.product(*[range(k) for k in n]):
+        x = list(x)
+        s = site(x)
+        ft = np.zeros(Q)
+        for i in range(Q):
+            src = [x[a] - e[i, a] for a in range(D)]
+            if 0 <= src[A] < n[A] or bc_wall == 0:
+                ft[i] = fstar[i, site([src[a] % n[a] for a in range(D)])]
+            elif bc_wall == 1:
+                # half-way bounce-back: the opposite population, same column
+                mir = e[i, A] - 1 - x[A] if src[A] < 0 else 2 * n[A] - 1 - src[A]
+                ft[i] = fstar[opp[i], site(x[:A] + [mir])]
+            else:
+                side = 0 if src[A] < 0 else 1
+                rw, f0w = rho_w[(side, tuple(x[:A]))]
+                ft[i] = rw * f0w[i]
+        gs = gg[:, s]
+        rho = ft.sum()
+        ut = ft @ xi / rho
+        u = ut + 0.5 * gs
+        theta = ((ft @ np.sum(xi * xi, axis=1)) / rho - ut @ ut) / D + gs @ gs / (4 * D)
+        f0 = feq_product(xi, w, rho, u, theta, neq)
+        F = force_shift(xi, w, rho, u, theta, gs, order)
+        out[:, s] = ft - (ft - f0) / tau + (1.0 - 0.5 / tau) * F
+    return out
+
+
+def start_state(lat, shape, seed, bc, T_lo, T_hi, g, order, tau):
+    """A non-trivial post-collision state: smooth random fields, two oracle steps."""
+    D = W.dims(lat)
+    N = int(np.prod(shape))
+    rho = 1.0 + 0.02 * (W.uniform(seed, 1, N) - 0.5)
+    u = 0.06 * (W.uniform(seed, 2, D * N).reshape(D, N) - 0.5)
+    T = 1.0 + 0.08 * (W.uniform(seed, 3, N) - 0.5)
+    sim = oracle.OracleSim(lat, *shape, tau, g, force_order=order, bc=bc, T_lo=T_lo, T_hi=T_hi)
+    sim.init(rho, u, T)
+    sim.step(2)
+    return sim
+
+
+CASES = [
+    # lattice, shape, force order, wall rule on the last axis
+    (oracle.D2Q37, (4, 4, 1), 2, 0),
+    (oracle.D2Q37, (5, 3, 1), 1, 0),
+    (oracle.D2Q37, (4, 4, 1), 0, 0),
+    (oracle.D2Q37, (5, 7, 1), 2, 1),
+    (oracle.D2Q37, (4, 7, 1), 2, 2),
+    (oracle.D3Q39, (4, 3, 4), 2, 0),
+    (oracle.D3Q39, (3, 4, 6), 1, 1),
+    (oracle.D3Q39, (3, 3, 7), 2, 2),
+]
+
+
+@pytest.mark.parametrize("lat,shape,order,wall", CASES)
+def test_one_step_equals_brute_force(lat, shape, order, wall):
+    D = W.dims(lat)
+    N = int(np.prod(shape))
+    tau = 0.85
+    g = 0.01 * (W.uniform(41, 4, D * N).reshape(D, N) - 0.5)
+    bc = [0, 0, 0]
+    T_lo, T_hi = [1.0, 1.0, 1.0], [1.0, 1.0, 1.0]
+    if wall:
+        bc[D - 1] = wall
+        T_lo[D - 1], T_hi[D - 1] = 1.04, 0.97
+    sim = start_state(lat, shape, 40 + order, bc, T_lo, T_hi, g, order, tau)
+    fstar = sim.get_state()
+    ref = brute_step(fstar, lat, shape, tau, g, order, wall, T_lo[D - 1], T_hi[D - 1])
+    sim.step(1)
+    got = sim.get_state()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-15)
+    # the update moved the state: the comparison is not of two copies
+    assert np.max(np.abs(got - fstar)) > 1e-4
