@@ -36,7 +36,7 @@ def _rank(rank, world, port, results):
 
 def test_two_gloo_ranks_take_the_slowest_rank():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         results = m.dict()
         mp.spawn(_rank, args=(2, port, results), nprocs=2, join=True)
         got = dict(results)
