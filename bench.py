@@ -62,11 +62,21 @@ def parse_args():
     return ap.parse_args()
 
 
+def code_tokens(text):
+    """C++/CUDA source without comments and with whitespace runs collapsed:
+    edits to comments leave a kernel's identity unchanged."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_sha():
+    """Identity of the kernel sources the committed ncu summaries were taken
+    on (their code, not their comments)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2302_04741_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2302_04741_gb300", "csrc", f)) as fh:
+            h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

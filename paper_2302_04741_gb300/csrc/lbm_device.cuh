@@ -172,14 +172,16 @@ __device__ __forceinline__ R edot(const R (&v)[3]) {
 
 // ------------------------------------------- population cache policies
 // A step reads each stored population once and the next step reads what
-// this one writes.  When the two population buffers are not much larger
-// than L2, loads marked evict-first in L2 (StepParams::l2_evict_first) let
-// the lines just read go before the lines just written, part of which the
-// next step then finds in L2: the 1024 x 512 D2Q37 step (2 x 77.6 MB in
-// FP32, L2 129 MB) went from 25.2 to 22.5 us in FP32 and from 20.3 to
-// 19.5 us in FP16.  On working sets of twice L2 and more the hint cost 4-8 %,
-// so the host sets the flag only below 1.5 times the L2 size.  The results
-// are bit-identical either way.
+// this one writes.  With loads marked evict-first in L2
+// (StepParams::l2_evict_first) the lines just read leave L2 before the lines
+// just written.  In one A/B on one GB300 the 1024 x 512 D2Q37 step
+// (2 x 77.6 MB in FP32, L2 129 MB) went from 25.2 to 22.5 us in FP32 and
+// from 20.3 to 19.5 us in FP16 when launched back to back; serialised
+// launches under a profiler showed no gain (the same DRAM reads, fewer
+// writes inside the launch), so the benefit comes from how consecutive steps
+// share L2 and DRAM.  On working sets of twice L2 and more the hint cost
+// 4-8 %, so the host sets the flag only below 1.5 times the L2 size.  The
+// results are bit-identical either way.
 template <class T>
 __device__ __forceinline__ T ld_pop_policy(const T* ptr, bool evict_first) {
   unsigned long long first, normal;
