@@ -83,6 +83,12 @@ void wall_equilibrium(double T, double* fwd, double* fw) {
   }
 }
 
+// The FP16 codec factors of the context's lattice for its current scale.
+void fp16_factors(lbm_ctx* c) {
+  if (c->lat == LBM_D2Q37) lbm::set_fp16_factors<lbm::D2Q37>(c->p);
+  else lbm::set_fp16_factors<lbm::D3Q39>(c->p);
+}
+
 template <class L>
 void wall_tables(StepParams& p, double T_lo, double T_hi) {
   const int A = L::D - 1;
@@ -489,6 +495,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   if (p.mu == 0.0) p.mu_f = 0.0f;
   for (int a = 0; a < 3; ++a) p.g0_f[a] = (float)p.g0[a];
   p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
+  fp16_factors(c);
   p.l2_evict_first = lbm::l2_evict_first_for(2 * fbytes, c->device);
   if (wall != lbm::W_NONE) {
     if (lat == LBM_D2Q37) wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
@@ -609,6 +616,7 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
     if (scale != c->p.h_scale) drop_graphs(c);  // captured launches hold the old scale
     c->p.h_scale = scale;
     c->p.h_inv_scale = std::ldexp(1.0f, -k);
+    fp16_factors(c);
   }
   LBM_CUDA(c, c->ops->init(c->opt.precision, 1, drho, du, dT, c->f[0], nullptr, c->opt.force_order, c->p, c->stream));
   // host arrays (staged or read in place) may be freed after return
@@ -883,6 +891,7 @@ int lbm_load(lbm_ctx* c, const char* path) {
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "checkpoint upload failed: %s", cudaGetErrorString(e));
   c->p.h_scale = hd.h_scale;
   c->p.h_inv_scale = hd.h_inv_scale;
+  fp16_factors(c);
   c->steps = hd.steps;
   c->initialised = true;
   lbm::batch_mark_dirty(c->batch);

@@ -41,6 +41,11 @@ struct StepParams {
   double wall_inv_den[2];
   float h_scale;      // FP16 codec scale s and 1/s
   float h_inv_scale;
+  // FP16 codec factors per direction, float(w_i) / s and float(1 / w_i) s
+  // (set_fp16_factors): a decode or encode is then one multiply by a kernel
+  // parameter instead of two
+  float h_dec[QMAX];
+  float h_enc[QMAX];
   int* err;           // set to 1 by a kernel whose bounded wait ran out
   double mu;          // > 0: constant dynamic viscosity, 1/omega = mu/(rho theta) + 1/2 per site
   // float copies for the float kernels (no FP64 conversion on their path)
@@ -235,19 +240,29 @@ template <> struct Codec<P_FP16S> {
   using R = float;
   template <class L, int I>
   __device__ __forceinline__ static R decode(T v, const StepParams& p) {
-    constexpr float w = float(L::W(I));
-    return __half2float(v) * (w * p.h_inv_scale);
+    return __half2float(v) * p.h_dec[I];
   }
   template <class L, int I>
   __device__ __forceinline__ static T encode(R d, const StepParams& p) {
-    constexpr float iw = float(1.0 / L::W(I));
-    return __float2half_rn(d * (iw * p.h_scale));
+    return __float2half_rn(d * p.h_enc[I]);
   }
   __device__ __forceinline__ static T load(const T* ptr, const StepParams& p) {
     return ld_pop_policy(ptr, p.l2_evict_first != 0);
   }
   __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
 };
+
+// The FP16 factors of a lattice for the scale in p (host side).  Both are
+// products of two floats, as the device formed them before they became
+// parameters, so the stored values are unchanged.
+template <class L>
+inline void set_fp16_factors(StepParams& p) {
+  for (int i = 0; i < QMAX; ++i) p.h_dec[i] = p.h_enc[i] = 0.0f;
+  for (int i = 0; i < L::Q; ++i) {
+    p.h_dec[i] = float(L::w[i]) * p.h_inv_scale;
+    p.h_enc[i] = float(1.0 / L::w[i]) * p.h_scale;
+  }
+}
 
 // Load modes of a population pull: LD_HINT the codec's load (float codecs:
 // the L2 policy of StepParams::l2_evict_first), LD_RO the plain read-only

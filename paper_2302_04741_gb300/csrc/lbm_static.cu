@@ -175,6 +175,8 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   } else {
     p.h_scale = p.h_inv_scale = 1.0f;
   }
+  if (lat == LBM_D2Q37) lbm::set_fp16_factors<lbm::D2Q37>(p);
+  else lbm::set_fp16_factors<lbm::D3Q39>(p);
   StaticScratch* s = nullptr;
   int rc = scratch_for_current_device(&s);
   if (rc) return rc;
