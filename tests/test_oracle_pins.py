@@ -665,3 +665,31 @@ def test_sigma_bar_vanishes_in_static_conduction():
     assert wall > 1e-5
     centre = np.max(np.abs(s[0, 0, ny // 2 - 2:ny // 2 + 2]))
     assert centre < 1e-4 * wall, (centre, wall)
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (128, 4, 1)), (oracle.D3Q39, (96, 4, 4))])
+def test_adiabatic_sound_speed(lat, shape):
+    """A small density wave in a fluid at rest oscillates at the adiabatic
+    sound speed sqrt(gamma theta) with gamma = (D + 2) / D (monatomic gas:
+    2 in 2-D, 5/3 in 3-D), not the isothermal sqrt(theta): a pin of the
+    thermal coupling of the whole update (equilibrium with its theta terms,
+    energy conservation).  The velocity's projection on sin(kx) is timed
+    between zero crossings, one period per wavelength L = n_x c."""
+    D = W.dims(lat)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    x = np.arange(N) % nx
+    c = oracle.lattice_info(lat)[2]
+    k = 2 * np.pi / nx
+    sim = make_sim(lat, shape, 0.6, np.zeros((D, N)))
+    sim.init(1.0 + 1e-4 * np.cos(k * x), np.zeros((D, N)), np.ones(N))
+    s = np.sin(k * x)
+    a = []
+    for _ in range(260):
+        a.append(sim.moments()[1][0] @ s / (s @ s))
+        sim.step(1)
+    a = np.array(a)
+    z = [t + a[t] / (a[t] - a[t + 1]) for t in range(1, len(a) - 1) if a[t] * a[t + 1] < 0]
+    cs = nx * c / (z[2] - z[0])
+    gamma = (D + 2) / D
+    assert abs(cs / np.sqrt(gamma) - 1) < 1e-3, (cs, np.sqrt(gamma))
