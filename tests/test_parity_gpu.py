@@ -575,3 +575,29 @@ def test_create_rejects_invalid_arguments(kw, why):
         _create(**kw)
     assert ei.value.status == lbm.LBM_EINVAL, why
     assert str(ei.value), why
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("lat,shape", [(W.D2Q37, (128, 4, 1)), (W.D3Q39, (96, 4, 4))])
+def test_adiabatic_sound_speed_on_gpu(lat, shape, precision):
+    """The CUDA path carries sound at the adiabatic speed sqrt((D + 2) / D)
+    (the oracle's pin of the same run): a 1e-4 density wave in a fluid at
+    rest, the velocity's projection on sin(kx) timed between zero crossings."""
+    D = W.dims(lat)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    x = np.arange(N) % nx
+    k = 2 * np.pi / nx
+    w = dict(lattice=lat, shape=shape, tau=0.6, g={"kind": W.G_UNIFORM, "g0": (0.0, 0.0, 0.0)},
+             precision=precision, force_order=2, bc=(0, 0, 0), T_lo=(1.0,) * 3, T_hi=(1.0,) * 3,
+             rho=1.0 + 1e-4 * np.cos(k * x), u=np.zeros((D, N)), T=np.ones(N), name="sound")
+    sim = lbm.Sim(w).init()
+    s = np.sin(k * x)
+    a = []
+    for _ in range(260):
+        a.append(sim.moments()[1][0] @ s / (s @ s))
+        sim.step(1)
+    a = np.array(a)
+    z = [t + a[t] / (a[t] - a[t + 1]) for t in range(1, len(a) - 1) if a[t] * a[t + 1] < 0]
+    cs = nx * sim.c / (z[2] - z[0])
+    assert abs(cs / np.sqrt((D + 2) / D) - 1) < 1e-3, cs
