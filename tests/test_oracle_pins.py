@@ -720,3 +720,29 @@ def test_adiabatic_sound_speed_and_damping(lat, shape, tau, theta0, tol):
     (A, G, w, p), _ = curve_fit(wave, t[5:], a[5:], p0=p0)
     nu = theta0 * (tau - 0.5)
     assert abs(G / (nu * k * k) - 1) < tol, (G, nu * k * k)
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.9])
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (64, 4, 1)), (oracle.D3Q39, (48, 4, 4))])
+def test_thermal_diffusion_mode(lat, shape, tau):
+    """A temperature wave at uniform pressure (rho = 1 / theta) is the
+    entropy mode: it does not propagate and decays at chi k^2 with the
+    thermal diffusivity chi = lambda / (rho c_p) = theta (tau-hat - 1/2),
+    i.e. Prandtl number 1 for the single-relaxation-time collision."""
+    D = W.dims(lat)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    x = np.arange(N) % nx
+    c = oracle.lattice_info(lat)[2]
+    k = 2 * np.pi / (nx * c)
+    cc = np.cos(2 * np.pi * x / nx)
+    T0 = 1.0 + 1e-4 * cc
+    sim = make_sim(lat, shape, tau, np.zeros((D, N)))
+    sim.init(1.0 / T0, np.zeros((D, N)), T0)
+    amp = []
+    for _ in range(401):
+        amp.append((sim.moments()[2] - 1.0) @ cc / (cc @ cc))
+        sim.step(1)
+    t = np.arange(len(amp))
+    rate = -np.polyfit(t[50:], np.log(np.array(amp)[50:]), 1)[0]
+    assert abs(rate / ((tau - 0.5) * k * k) - 1) < 0.01, rate
