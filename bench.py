@@ -18,6 +18,7 @@ no data-path collective); the timing is the max over ranks.
 oracle LBM step over the same grid per benchmark step).
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -26,6 +27,7 @@ import re
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 import numpy as np
@@ -155,6 +157,71 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML (libnvidia-ml,
+    read-only queries) from a thread every few milliseconds: a timed region
+    of a few tens of milliseconds is shorter than nvidia-smi's sampling
+    period.  start() returns False when NVML cannot be used."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, index, period=0.005):
+        self.index = index
+        self.period = period
+        self.lib = None
+        self.handle = None
+        self.max_mhz = None
+        self.thread = None
+        self.running = False
+        self.samples = []
+
+    def start(self):
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            lib.nvmlInit_v2.restype = ctypes.c_int
+            if lib.nvmlInit_v2() != 0:
+                return False
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h)) != 0:
+                return False
+            self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) != 0:
+                return False
+        except (OSError, AttributeError):
+            return False
+        self.lib, self.handle, self.max_mhz = lib, h, mx.value
+        self.running = True
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+        return True
+
+    def _loop(self):
+        clk, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+        while self.running:
+            if (self.lib.nvmlDeviceGetClockInfo(self.handle, ctypes.c_int(1), ctypes.byref(clk)) == 0
+                    and self.reason_fn(self.handle, ctypes.byref(rs)) == 0):
+                self.samples.append((clk.value, rs.value))
+            time.sleep(self.period)
+
+    def stop(self):
+        if not self.thread:
+            return None
+        self.running = False
+        self.thread.join(timeout=2)
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+        if not self.samples:
+            return None
+        reasons = sorted({n for _, r in self.samples for bit, n in self.REASONS.items() if r & bit})
+        return {"sm_mhz": float(np.median([c for c, _ in self.samples])), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(self.samples), "source": "nvml, 5 ms"}
 
 
 def aggregate_ranks(elapsed_ms, units_per_rank, world, device=None):
@@ -423,8 +490,10 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks = NvmlSampler(local)
+    if not clocks.start():
+        clocks = ClockSampler(local)
+        clocks.start()
     total_ms, kern_ms, launches = time_context(lbm, torch, sim, stream, flush, K, Wm, inner)
     barrier()
     clk = clocks.stop()
