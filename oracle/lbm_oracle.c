@@ -40,7 +40,11 @@
  *       keeping the column, f~_i(x) = f*_{-i}(x with x_a -> e_ia - 1 - x_a)
  *       at the low wall (mirrored at the high wall); the thermal wall fills
  *       the same slots with rho_w f0_i(1, 0, T_wall) where rho_w makes the
- *       column's incoming mass equal its outgoing mass.
+ *       column's incoming mass equal its outgoing mass.  Pinned by mass
+ *       conservation, the conduction profile, Fourier's law, the no-slip
+ *       channel parabola and the kinetic slip; the exact slot values in the
+ *       first rows are parity unpinned (only a loop restatement of this
+ *       reading checks them), as for R15.
  *   R11 storage holds the post-collision distribution f*; a step pulls
  *       f~_i(x) = f*_i(x - e_i) and collides.  init places f~ = f0 - F/2 at
  *       the slots the first pull reads, so the pulled state at t = 0 is
