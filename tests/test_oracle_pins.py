@@ -746,3 +746,33 @@ def test_thermal_diffusion_mode(lat, shape, tau):
     t = np.arange(len(amp))
     rate = -np.polyfit(t[50:], np.log(np.array(amp)[50:]), 1)[0]
     assert abs(rate / ((tau - 0.5) * k * k) - 1) < 0.01, rate
+
+
+@pytest.mark.parametrize("lat,shape", [(oracle.D2Q37, (64, 4, 1)), (oracle.D3Q39, (48, 4, 4))])
+def test_galilean_invariance_of_a_shear_wave(lat, shape):
+    """A shear wave u_y = A sin(kx) on a uniform stream u_x = U0 is carried
+    along at U0 (its phase advances by k U0 t) and decays at the same rate as
+    at rest: the viscosity seen by the wave does not depend on the frame
+    (Galilean invariance of the high-order equilibrium)."""
+    D = W.dims(lat)
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    x = np.arange(N) % nx
+    c = oracle.lattice_info(lat)[2]
+    k = 2 * np.pi / (nx * c)
+    A, T, tau = 1e-4, 150, 0.8
+    wave = np.exp(-1j * 2 * np.pi * x / nx)
+    amp = {}
+    for U0 in (0.0, 0.1, 0.2):
+        u = np.zeros((D, N))
+        u[0] = U0
+        u[1] = A * np.sin(2 * np.pi * x / nx)
+        sim = make_sim(lat, shape, tau, np.zeros((D, N)))
+        sim.init(np.ones(N), u, np.ones(N))
+        sim.step(T)
+        z = sim.moments()[1][1] @ wave / (N / 2) / (-1j * A)   # = exp(-Gamma T - i k U0 T)
+        amp[U0] = abs(z)
+        assert abs(np.angle(z * np.exp(1j * k * U0 * T))) < 1e-4, (U0, np.angle(z))
+    assert abs(amp[0.0] - np.exp(-(tau - 0.5) * k * k * T)) < 1e-2 * (1 - amp[0.0])
+    for U0 in (0.1, 0.2):
+        assert abs(amp[U0] / amp[0.0] - 1) < 1e-4, (U0, amp)
