@@ -58,11 +58,16 @@ def feq_product(xi, w, rho, u, theta, neq):
     return w * out
 
 
-def force_shift(xi, w, rho, u, theta, g, order):
+def force_shift(xi, w, rho, u, theta, g, order, sigma=None):
+    """sigma (D x D): the non-equilibrium stress, subtracted from the
+    second-order coefficients (a^(2) = a^(2)_0 - sigma-bar, Eq. f2)."""
     D = xi.shape[1]
     out = np.zeros(len(w))
     for m in multi_indices(D, order):
         coef = rho * np.prod([he_mean(m[b], u[b], theta) / math.factorial(m[b]) for b in range(D)])
+        if sigma is not None and sum(m) == 2:
+            ab = [b for b in range(D) for _ in range(m[b])]        # the tensor index pair
+            coef -= sigma[ab[0], ab[1]] / np.prod([math.factorial(m[b]) for b in range(D)])
         for a in range(D):
             mm = list(m)
             mm[a] += 1
@@ -71,12 +76,15 @@ def force_shift(xi, w, rho, u, theta, g, order):
 
 
 def brute_step(fstar, lat, shape, tau, g, order, bc_wall=0, T_lo=1.0, T_hi=1.0, solid=None,
-               T_wall=None):
+               T_wall=None, sigma=False, mu=0.0):
     """One step of Eq. lbm from the post-collision state fstar (Q, N).
     bc_wall: 0 periodic, 1 bounce-back, 2 thermal wall on the last axis.
     solid (N flags) with T_wall (N): staircase diffuse walls on a periodic
     grid -- a fluid site re-emits the mass it sends into solid sites as wall
-    Maxwellians at the temperatures of the solid sites it pulls from."""
+    Maxwellians at the temperatures of the solid sites it pulls from.
+    sigma: the force's second-order coefficients less the non-equilibrium
+    stress sigma-bar = -(1 - 1/(2 tau)) sum (f~ - f0)(xi - u)(xi - u);
+    mu > 0: each site relaxes with tau-hat = mu / (rho theta) + 1/2."""
     D, Q, c, e, w, neq = oracle.lattice_info(lat)
     e = e[:, :D]
     xi = c * e.astype(float)
@@ -143,8 +151,13 @@ def brute_step(fstar, lat, shape, tau, g, order, bc_wall=0, T_lo=1.0, T_hi=1.0, 
         u = ut + 0.5 * gs
         theta = ((ft @ np.sum(xi * xi, axis=1)) / rho - ut @ ut) / D + gs @ gs / (4 * D)
         f0 = feq_product(xi, w, rho, u, theta, neq)
-        F = force_shift(xi, w, rho, u, theta, gs, order)
-        out[:, s] = ft - (ft - f0) / tau + (1.0 - 0.5 / tau) * F
+        tau_s = mu / (rho * theta) + 0.5 if mu > 0 else tau
+        sig = None
+        if sigma:
+            cc = xi - u
+            sig = -(1.0 - 0.5 / tau_s) * np.einsum("i,ia,ib->ab", ft - f0, cc, cc)
+        F = force_shift(xi, w, rho, u, theta, gs, order, sig)
+        out[:, s] = ft - (ft - f0) / tau_s + (1.0 - 0.5 / tau_s) * F
     return out
 
 
@@ -225,3 +238,39 @@ def test_one_step_with_solid_sites_equals_brute_force(lat, shape):
     fluid = solid == 0
     np.testing.assert_allclose(got[:, fluid], ref[:, fluid], rtol=0, atol=2e-15)
     assert np.max(np.abs(got[:, fluid] - fstar[:, fluid])) > 1e-4
+
+
+@pytest.mark.parametrize("lat,shape,wall,sigma,mu", [
+    (oracle.D2Q37, (5, 4, 1), 0, True, 0.0),
+    (oracle.D2Q37, (4, 7, 1), 2, False, 0.05),
+    (oracle.D2Q37, (4, 7, 1), 2, True, 0.05),
+    (oracle.D3Q39, (4, 3, 4), 0, True, 0.08),
+])
+def test_one_step_with_sigma_and_constant_mu_equals_brute_force(lat, shape, wall, sigma, mu):
+    """The sigma-bar terms of Eq. fi (R8: sigma-bar from the pulled f~ about
+    the mid-point velocity, entering the second-order coefficients of the
+    n = 3 force term) and the constant-viscosity relaxation (R13:
+    tau-hat = mu / (rho theta) + 1/2 per site), in the same restatement."""
+    D = W.dims(lat)
+    N = int(np.prod(shape))
+    tau, order = 0.85, 2
+    g = 0.01 * (W.uniform(45, 4, D * N).reshape(D, N) - 0.5)
+    bc = [0, 0, 0]
+    T_lo, T_hi = [1.0, 1.0, 1.0], [1.0, 1.0, 1.0]
+    if wall:
+        bc[D - 1] = wall
+        T_lo[D - 1], T_hi[D - 1] = 1.04, 0.97
+    rho = 1.0 + 0.02 * (W.uniform(46, 1, N) - 0.5)
+    u = 0.06 * (W.uniform(46, 2, D * N).reshape(D, N) - 0.5)
+    T = 1.0 + 0.08 * (W.uniform(46, 3, N) - 0.5)
+    sim = oracle.OracleSim(lat, *shape, tau, g, force_order=order, include_sigma=sigma, bc=bc,
+                           T_lo=T_lo, T_hi=T_hi, mu=mu)
+    sim.init(rho, u, T)
+    sim.step(2)
+    fstar = sim.get_state()
+    ref = brute_step(fstar, lat, shape, tau, g, order, wall, T_lo[D - 1], T_hi[D - 1],
+                     sigma=sigma, mu=mu)
+    sim.step(1)
+    got = sim.get_state()
+    np.testing.assert_allclose(got, ref, rtol=0, atol=2e-15)
+    assert np.max(np.abs(got - fstar)) > 1e-4
