@@ -14,9 +14,11 @@ route that shares nothing with the oracle's tensor code:
   F_i = w_i rho sum_a g_a sum_{|m| <= N} prod_b E[He_{m_b}] / m_b! He_{m + e_a}(xi_i);
 * the mid-point state of Sec. 2 (u = j / rho + g / 2, theta with the g^2 / 4D
   term) and the pull with the wall rules written as loops over sites and
-  directions: half-way bounce-back in the same column, and the diffuse
-  thermal wall that re-emits, per column, the mass leaving through the wall
-  as a wall Maxwellian.
+  directions: half-way bounce-back in the same column, the diffuse thermal
+  wall that re-emits, per column, the mass leaving through the wall as a
+  wall Maxwellian, and solid sites that do the same per fluid site;
+* optionally the sigma-bar terms (subtracted from the second-order
+  coefficients of the force) and the constant-viscosity relaxation time.
 
 Everything is FP64 on both sides; only the summation order differs.
 """
