@@ -608,3 +608,30 @@ def test_adiabatic_sound_speed_on_gpu(lat, shape, precision):
     z = [t + a[t] / (a[t] - a[t + 1]) for t in range(1, len(a) - 1) if a[t] * a[t + 1] < 0]
     cs = nx * sim.c / (z[2] - z[0])
     assert abs(cs / np.sqrt((D + 2) / D) - 1) < 1e-3, cs
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-4), (1, 1e-3)])
+def test_galilean_invariance_on_gpu(precision, tol):
+    """A shear wave u_y = A sin(kx) on a stream U0 = 0.2 (D2Q37): the CUDA
+    path carries it at U0 and damps it as at rest (the oracle's pin of the
+    same run), in FP64 and in FP32-shifted storage."""
+    lat, shape = W.D2Q37, (64, 4, 1)
+    D, N = 2, 256
+    x = np.arange(N) % 64
+    A, T = 1e-4, 150
+    amp = {}
+    for U0 in (0.0, 0.2):
+        u = np.zeros((D, N))
+        u[0] = U0
+        u[1] = A * np.sin(2 * np.pi * x / 64)
+        w = dict(lattice=lat, shape=shape, tau=0.8, g={"kind": W.G_UNIFORM, "g0": (0.0, 0.0, 0.0)},
+                 precision=precision, force_order=2, bc=(0, 0, 0), T_lo=(1.0,) * 3,
+                 T_hi=(1.0,) * 3, rho=np.ones(N), u=u, T=np.ones(N), name="shear")
+        sim = lbm.Sim(w).init()
+        k = 2 * np.pi / (64 * sim.c)
+        sim.step(T)
+        z = sim.moments()[1][1] @ np.exp(-1j * 2 * np.pi * x / 64) / (N / 2) / (-1j * A)
+        amp[U0] = abs(z)
+        assert abs(np.angle(z * np.exp(1j * k * U0 * T))) < tol, (U0, np.angle(z))
+        sim.close()
+    assert abs(amp[0.2] / amp[0.0] - 1) < tol, amp
