@@ -276,3 +276,43 @@ def test_one_step_with_sigma_and_constant_mu_equals_brute_force(lat, shape, wall
     got = sim.get_state()
     np.testing.assert_allclose(got, ref, rtol=0, atol=2e-15)
     assert np.max(np.abs(got - fstar)) > 1e-4
+
+
+@pytest.mark.parametrize("lat,shape,order,mu", [
+    (oracle.D2Q37, (4, 4, 1), 2, 0.0),
+    (oracle.D2Q37, (5, 3, 1), 1, 0.0),
+    (oracle.D2Q37, (4, 4, 1), 0, 0.05),
+    (oracle.D3Q39, (4, 3, 4), 2, 0.08),
+])
+def test_moments_equal_brute_force(lat, shape, order, mu):
+    """The diagnostics of the oracle (rho, u, T at the mid-point, R1, and the
+    heat flux of R9, q = 1/2 (1 - 1/(2 tau)) sum (f~ - f0 + F/2) |xi - u|^2
+    (xi - u)) recomputed from the pulled state by the same product-form
+    equilibrium and index-shift force."""
+    D, Q, c, e, w, neq = oracle.lattice_info(lat)
+    xi = c * e[:, :D].astype(float)
+    N = int(np.prod(shape))
+    tau = 0.85
+    g = 0.01 * (W.uniform(47, 4, D * N).reshape(D, N) - 0.5)
+    rho0 = 1.0 + 0.02 * (W.uniform(48, 1, N) - 0.5)
+    u0 = 0.06 * (W.uniform(48, 2, D * N).reshape(D, N) - 0.5)
+    T0 = 1.0 + 0.08 * (W.uniform(48, 3, N) - 0.5)
+    sim = oracle.OracleSim(lat, *shape, tau, g, force_order=order, mu=mu)
+    sim.init(rho0, u0, T0)
+    sim.step(3)
+    ft = sim.pulled()
+    rho, u, T, q = sim.moments()
+    for s in range(N):
+        f = ft[:, s]
+        r = f.sum()
+        ut = f @ xi / r
+        uu = ut + 0.5 * g[:, s]
+        th = ((f @ np.sum(xi * xi, axis=1)) / r - ut @ ut) / D + g[:, s] @ g[:, s] / (4 * D)
+        tau_s = mu / (r * th) + 0.5 if mu > 0 else tau
+        f0 = feq_product(xi, w, r, uu, th, neq)
+        F = force_shift(xi, w, r, uu, th, g[:, s], order)
+        cc = xi - uu
+        qq = 0.5 * (1.0 - 0.5 / tau_s) * ((f - f0 + 0.5 * F) * np.sum(cc * cc, axis=1)) @ cc
+        assert abs(rho[s] - r) < 1e-15 and abs(T[s] - th) < 1e-15
+        np.testing.assert_allclose(u[:, s], uu, rtol=0, atol=1e-16)
+        np.testing.assert_allclose(q[:, s], qq, rtol=0, atol=1e-15)
