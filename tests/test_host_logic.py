@@ -53,3 +53,21 @@ def test_nvidia_smi_sampler_parses_its_csv(tmp_path):
     assert out["samples"] == 2 and out["sm_max_mhz"] == 2070.0
     assert out["sm_mhz"] == 2025.0
     assert out["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_profiled_traffic_needs_the_current_kernel_sources(tmp_path, monkeypatch):
+    """The committed ncu traffic is reported only while its kernel_source_sha
+    matches the kernel sources' code."""
+    sha = bench.kernel_source_sha()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "ok.md").write_text(
+        f"table\ntraffic_bytes_per_launch: 12345\nkernel_source_sha: {sha}\n")
+    (tmp_path / "profiles" / "stale.md").write_text(
+        "traffic_bytes_per_launch: 12345\nkernel_source_sha: 0123456789abcdef\n")
+    real_root = bench.ROOT
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: sha)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("ok.md") == 12345.0
+    assert bench.profiled_traffic("stale.md") is None
+    assert bench.profiled_traffic("missing.md") is None
+    monkeypatch.setattr(bench, "ROOT", real_root)
