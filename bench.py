@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & % HBM roofline, FP32-shifted vs FP64 at stated L2 error; serving p50/p99"
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_tma.cuh", "lbm_async.cuh",
-                  "lattice_tables.cuh"]
+                  "lbm_wave.cuh", "lbm_batch.cuh", "lbm_launch.cuh", "lattice_tables.cuh"]
 
 
 def parse_args():
@@ -61,6 +61,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other configurations (Kolmogorov, ragged batch, serving, 3-D FP16)")
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the full-length FP32 accuracy runs (three 20k-step FP64 runs)")
     return ap.parse_args()
 
 
@@ -309,16 +311,6 @@ def run_reference(args):
 
 
 # ------------------------------------------------------ other configurations
-def rel_errors(a, b):
-    """Relative L2 of (rho, u, T, q); q normalised by max(||q_b||, 1e-3 Ma sqrt(size))."""
-    qf = 1e-3 * max(float(np.abs(b[1]).max()), 1e-3) * math.sqrt(b[1].size)
-    out = {}
-    for nm, x, y in zip(("rho", "u", "T", "q"), a, b):
-        fl = qf if nm == "q" else 0.0
-        out[nm] = float(np.linalg.norm(x - y) / max(np.linalg.norm(y), fl))
-    return out
-
-
 def event_time(torch, stream, fn, reps):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -419,16 +411,12 @@ def extra_rb3d(lbm, torch, W, peak, K=20, err_steps=100):
     t = event_time(torch, stream, lambda: a.step(1), K)
     mlups = N * K / t / 1e6
     a.close()
-    a = lbm.Sim(w16, stream=stream.cuda_stream).init()
-    b = lbm.Sim(dict(w16, precision=W.FP64), stream=stream.cuda_stream).init()
-    a.step(err_steps)
-    b.step(err_steps)
-    errs = rel_errors(a.moments(), b.moments())
-    a.close()
-    b.close()
+    from paper_2302_04741_gb300 import accuracy as A
+    acc = A.codec_accuracy(w16, W.FP16_SCALED, [err_steps], stream=stream.cuda_stream,
+                           runs=("codec", "floor"))[err_steps]
     return {"workload": "rayleigh_benard_d3q39_512x512x256_fp16", "sites": N, "mlups": mlups,
             "roofline_frac": mlups * 1e6 * 156 / (peak * 1e9),
-            "l2_vs_fp64_gpu": dict(steps=err_steps, **errs)}
+            "l2_vs_fp64_gpu": dict(steps=err_steps, **acc["codec"], storage_floor=acc["floor"])}
 
 
 # --------------------------------------------------------------- our arm
@@ -523,21 +511,19 @@ def run_ours(args):
         extra["fp64"] = {"value": v64, "unit": "MLUPS", "roofline_frac_hbm": a64 / peak,
                          "achieved_gbs": a64, "ratio_fp32_over_fp64": value / world / v64}
         sim64.close()
-        # accuracy of the FP32-shifted state against the FP64 state, same steps
-        acc_steps = 1000
-        a = lbm.Sim(w32, stream=stream.cuda_stream).init()
-        b = lbm.Sim(w64, stream=stream.cuda_stream).init()
-        a.step(acc_steps)
-        b.step(acc_steps)
-        ma, mb = a.moments(), b.moments()
-        qf = 1e-3 * max(float(np.abs(mb[1]).max()), 1e-3) * math.sqrt(mb[1].size)
-        errs = {}
-        for nm, x, y in zip(("rho", "u", "T", "q"), ma, mb):
-            fl = qf if nm == "q" else 0.0
-            errs[nm] = float(np.linalg.norm(x - y) / max(np.linalg.norm(y), fl))
-        extra["l2_fp32_vs_fp64_gpu"] = {"steps": acc_steps, **errs}
-        a.close()
-        b.close()
+        # accuracy of the FP32-shifted run against the FP64 run over the
+        # configuration's full 20k steps, with the FP64 butterfly floor and the
+        # FP32 storage floor (paper_2302_04741_gb300.accuracy)
+        from paper_2302_04741_gb300 import accuracy as A
+        if not args.no_accuracy:
+            acc = A.codec_accuracy(w32, W.FP32_SHIFTED, [1000, 20000], stream=stream.cuda_stream,
+                                   graph_steps=args.graph_steps)
+            extra["l2_fp32_vs_fp64_gpu"] = {
+                "steps": 20000, **acc[20000]["codec"], "at_1000_steps": acc[1000]["codec"],
+                "butterfly_floor": acc[20000]["butterfly"], "storage_floor": acc[20000]["floor"],
+                "note": "relative L2 against the FP64 GPU run of the same grid (itself oracle-checked); "
+                        "butterfly = FP64 with a 1e-15 initial perturbation; storage floor = FP64 "
+                        "arithmetic with FP32 storage rounding"}
 
     # end to end: host arrays in, moments out, through the C ABI
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()

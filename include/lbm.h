@@ -135,6 +135,15 @@ typedef struct {
                         LBM_OVERLAP_MIN_SITES sites (on grids too small to
                         fill the GPU its effect was within run-to-run noise).
                         Results are identical either way.                    */
+  int storage_probe; /* LBM_FP64 storage only: 0 (default) off; LBM_FP32_SHIFTED
+                        or LBM_FP16_SCALED: after every step (and at lbm_init)
+                        each stored deviation f*_i - w_i is rounded to that
+                        codec's format (float; half of s (f - w)/w with the
+                        scale s chosen at lbm_init as for LBM_FP16_SCALED),
+                        the arithmetic staying in double.  Such a run has the
+                        storage precision of the named codec and exact
+                        arithmetic: its distance from the plain FP64 run is
+                        the codec's storage floor.  Plain step kernel only.  */
 } lbm_options;
 
 #define LBM_OVERLAP_MIN_SITES 131072
@@ -164,10 +173,15 @@ size_t lbm_options_size(void);
 int lbm_lattice_info(lbm_lattice lat, int *D, int *Q, double *c, int *e, double *w);
 
 /* Creates a context on the current CUDA device for an nx*ny*nz grid (nz must
- * be 1 on D2Q37).  tau is the collision divisor tau-hat > 1/2.  g may be NULL
- * (no force).  opt may be NULL (defaults).  Allocates two population buffers
- * (ping-pong), the force table and reduction scratch.  *out receives the
- * context, or NULL on error. */
+ * be 1 on D2Q37): the discrete problem of Sec. 2 -- the distribution f_i on
+ * the Gauss-Hermite abscissae xi_i = c e_i (Eq. rut1 and the quadrature that
+ * precedes it), advanced by Eq. lbm with collision divisor tau = tau-hat
+ * > 1/2 and the body-force acceleration g of Eq. BGK.  g may be NULL (no
+ * force).  opt may be NULL (defaults).  Allocates two population buffers
+ * (ping-pong), the force table and reduction scratch; the context owns them
+ * until lbm_destroy.  *out receives the context, or NULL on error
+ * (LBM_EINVAL for an invalid argument, checked before any allocation;
+ * LBM_ENOMEM / LBM_ECUDA when the device refuses). */
 int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gfield *g,
                const lbm_options *opt, lbm_ctx **out);
 
@@ -199,8 +213,13 @@ int lbm_init(lbm_ctx *ctx, const double *rho, const double *u, const double *T);
  * lbm_load. */
 int lbm_set_solid(lbm_ctx *ctx, const unsigned char *solid, const double *T_wall);
 
-/* Advances n >= 0 steps (one fused pull-stream + collide launch per step, or
- * graph replays).  Asynchronous on the context's stream. */
+/* Advances n >= 0 steps of Eq. lbm (Sec. 2): per step and site, the pull
+ * f~_i(x) = f*_i(x - e_i), the moments of Eq. rut1, the mid-point state
+ * rho, u + g/2, theta, the equilibrium (Eq. fN with the Maxwellian
+ * coefficients) and the force of Eq. fi, and the relaxation
+ * f*_i = f~_i - (f~_i - f0_i)/tau + (1 - 1/(2 tau)) F_i -- one fused launch
+ * per step, or graph replays.  Asynchronous on the context's stream.
+ * LBM_EINVAL for n < 0, LBM_ESTATE before lbm_init or on a batch member. */
 int lbm_step(lbm_ctx *ctx, int n);
 
 /* Physical mid-point moments of the current state, in double: rho (N),
@@ -212,9 +231,11 @@ int lbm_step(lbm_ctx *ctx, int n);
  * device buffer.  Synchronises the stream. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *q);
 
-/* Global sums over the grid (deterministic for a fixed grid): mass =
- * sum rho, mom[D] = sum rho u, energy = sum rho (|u|^2 + D theta)/2, all
- * physical mid-point values.  Per-site moments and the compensated
+/* Global sums over the grid (deterministic for a fixed grid) of the
+ * conserved moments of Eq. rut (discrete form Eq. rut1): mass = sum rho,
+ * mom[D] = sum rho u, energy = sum rho (|u|^2 + D theta)/2, all physical
+ * mid-point values (with a force, Eq. lbm changes the momentum by sum rho g
+ * and the energy by sum rho g.u per step, Sec. 2).  Per-site moments and the compensated
  * (two-sum) per-thread, block and grid merges run in the storage's
  * arithmetic precision (double for LBM_FP64, float pairs otherwise, about
  * 48 bits), in a fixed order; the totals are combined in double.  Any output
@@ -256,8 +277,10 @@ size_t lbm_device_bytes(const lbm_ctx *ctx);
  * call made without a context: lbm_create, lbm_conserved_static).  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
-/* Frees all device memory of the context and the context itself.  NULL is a
- * no-op. */
+/* Frees all device memory of the context (the populations of Eq. lbm, the
+ * force table and the reduction scratch allocated by lbm_create) and the
+ * context itself, after the context's stream has drained; a batch member is
+ * removed from its batch first.  NULL is a no-op.  Never fails. */
 void lbm_destroy(lbm_ctx *ctx);
 
 /* ---- Batches: many grids, one launch per step. ----
@@ -305,6 +328,61 @@ int lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_x, int *sites_per_t
 const char *lbm_batch_last_error(const lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);
 
+/* ---- Slabs: one grid split along its last axis. ----
+ *
+ * Eq. lbm is local (Sec. 2): a step at site x reads f*_i(x - e_i) with
+ * |e_ia| <= 3, so a grid cut into slabs of its last axis (y on D2Q37, z on
+ * D3Q39) steps each slab on its own once the three layers beyond each cut
+ * are known.  A slab context holds global layers [a_begin, a_end) of that
+ * axis plus three ghost layers on each side that is not a wall (a periodic
+ * axis wraps: the first slab's lower neighbour is the last slab).  Per step:
+ * lbm_step on every slab, then one halo exchange per cut, which copies into
+ * each neighbour's ghost layers the planes its sites pull (populations
+ * pointing across the cut, up to three layers deep).  The slabs then
+ * reproduce the undivided grid bit for bit (same kernels, same inputs).
+ *
+ * lbm_create_slab: nx, ny, nz, tau, g and opt as for lbm_create on the
+ *   whole grid; 0 <= a_begin < a_end <= n_axis, at least 3 layers.  Caller
+ *   arrays of lbm_init, lbm_moments, lbm_get_populations, lbm_get_state and
+ *   lbm_set_state, and an LBM_G_FIELD force, cover the slab's own layers only
+ *   (N_slab = nx * (a_end - a_begin) sites on D2Q37, nx * ny * (a_end -
+ *   a_begin) on D3Q39, same layouts); lbm_conserved sums the slab's own
+ *   sites.  Plain step kernel, graph_steps = 0 (a step is followed by an
+ *   exchange), no solid sites, no batches.  After lbm_init no exchange is
+ *   needed before the first step (the init writes every slot the slab's
+ *   sites pull); after lbm_set_state or lbm_load of a single slab, exchange
+ *   before stepping.  LBM_EINVAL on a bad range or option.
+ * lbm_slab_exchange: both directions of the cut between lo and hi (hi holds
+ *   the layers after lo's, or lo ends the axis and hi starts it on a
+ *   periodic axis); same device, issued on lo's stream (order the two
+ *   slabs' steps before it, e.g. one stream for all slabs).  FP16 slabs must
+ *   share one scale (lbm_set_fp16_scale).
+ * lbm_slab_halo_pack / unpack: the same exchange through a message, for
+ *   slabs on different devices or processes (the caller moves the message,
+ *   e.g. with NCCL send / recv): pack side 1 writes the message for the
+ *   neighbour above, side 0 for the one below; unpack side 0 reads the
+ *   message from the neighbour below, side 1 from above.  The message is
+ *   lbm_slab_halo_bytes(ctx) bytes of device memory (same on both sides of a
+ *   cut); asynchronous on the slab's stream.  LBM_EINVAL when the side is a
+ *   wall.
+ * lbm_slab_info: the slab's range and ghost layers (a whole-grid context
+ *   reports [0, n_axis) and no ghosts). */
+int lbm_create_slab(lbm_lattice lat, int nx, int ny, int nz, int a_begin, int a_end, double tau,
+                    const lbm_gfield *g, const lbm_options *opt, lbm_ctx **out);
+int lbm_slab_exchange(lbm_ctx *lo, lbm_ctx *hi);
+size_t lbm_slab_halo_bytes(const lbm_ctx *ctx);
+int lbm_slab_halo_pack(lbm_ctx *ctx, int side, void *dst);
+int lbm_slab_halo_unpack(lbm_ctx *ctx, int side, const void *src);
+int lbm_slab_info(const lbm_ctx *ctx, int *a_begin, int *a_end, int *ghosts_below, int *ghosts_above);
+
+/* Sets the FP16 scale s of an initialised LBM_FP16_SCALED context to a power
+ * of two, rescaling the stored half values exactly (a power-of-two factor
+ * only shifts their exponents; values that leave the normal half range are
+ * rounded).  Used to give FP16 slabs of one grid the scale the undivided
+ * grid would choose (the smallest of their own).  LBM_EINVAL for another
+ * codec or a scale that is not a power of two. */
+int lbm_set_fp16_scale(lbm_ctx *ctx, double scale);
+
 /* ---- Allocation-free conservation sums (no counterpart in the paper). ----
  *
  * For callers that must not allocate device memory: a plugin inside an
@@ -324,6 +402,14 @@ void lbm_batch_destroy(lbm_batch *b);
  *        doubles (LBM_G_SINE is rejected: pass it as a field);
  *   out  device pointer to 6 doubles: mass, momentum[3], energy, and the
  *        number of sites with a non-finite moment, rho <= 0 or T <= 0.
+ *
+ * Solid sites (lbm_set_solid) are not supported: every site is summed as
+ * fluid and pulled with the plain rule, so on a state from a context with
+ * solid sites the sums differ from lbm_conserved.
+ *
+ * f, out and a field force must be device (or managed) memory of the
+ * current device; host addresses and memory of another GPU are rejected with
+ * LBM_EINVAL before any launch.
  *
  * Nothing is allocated: the per-block partial sums live in a static device
  * array of LBM_STATIC_MAX_TILES row tiles (128 sites along x each; 3.0 MB

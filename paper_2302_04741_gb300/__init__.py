@@ -44,7 +44,7 @@ class lbm_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("block_x", ctypes.c_int),
                 ("graph_steps", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("tma_stages", ctypes.c_int), ("mu", ctypes.c_double),
-                ("overlap_steps", ctypes.c_int)]
+                ("overlap_steps", ctypes.c_int), ("storage_probe", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -114,6 +114,17 @@ def lib():
         L.lbm_batch_last_error.restype = ctypes.c_char_p
         L.lbm_batch_destroy.argtypes = [_vp]
         L.lbm_batch_destroy.restype = None
+        L.lbm_create_slab.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.POINTER(lbm_gfield), ctypes.POINTER(lbm_options),
+                                      ctypes.POINTER(_vp)]
+        L.lbm_slab_exchange.argtypes = [_vp, _vp]
+        L.lbm_slab_halo_bytes.argtypes = [_vp]
+        L.lbm_slab_halo_bytes.restype = ctypes.c_size_t
+        L.lbm_slab_halo_pack.argtypes = [_vp, ctypes.c_int, _vp]
+        L.lbm_slab_halo_unpack.argtypes = [_vp, ctypes.c_int, _vp]
+        L.lbm_slab_info.argtypes = [_vp] + [ctypes.POINTER(ctypes.c_int)] * 4
+        L.lbm_set_fp16_scale.argtypes = [_vp, ctypes.c_double]
         L.lbm_conserved_static.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                            ctypes.POINTER(lbm_options), ctypes.POINTER(lbm_gfield),
                                            ctypes.c_double, _vp, _vp]
@@ -269,6 +280,45 @@ def lbm_conserved_static(lat, nx, ny, nz, opt, g, fp16_scale, f, out):
                                       float(fp16_scale), fp, op))
 
 
+def lbm_create_slab(lat, nx, ny, nz, a_begin, a_end, tau, g=None, opt=None):
+    """Slab [a_begin, a_end) of the last axis of an nx x ny x nz grid (see include/lbm.h)."""
+    ctx = _vp()
+    gf = make_gfield(g) if isinstance(g, dict) else g
+    rc = lib().lbm_create_slab(lat, nx, ny, nz, a_begin, a_end, tau,
+                               ctypes.byref(gf) if gf is not None else None,
+                               ctypes.byref(opt) if opt is not None else None, ctypes.byref(ctx))
+    _check(rc)
+    return ctx
+
+
+def lbm_slab_exchange(lo, hi):
+    _check(lib().lbm_slab_exchange(lo, hi), lo)
+
+
+def lbm_slab_halo_bytes(ctx):
+    return int(lib().lbm_slab_halo_bytes(ctx))
+
+
+def lbm_slab_halo_pack(ctx, side, dst):
+    """dst: device pointer (int) or CUDA tensor of lbm_slab_halo_bytes(ctx) bytes."""
+    _check(lib().lbm_slab_halo_pack(ctx, int(side), dst.data_ptr() if hasattr(dst, "data_ptr") else dst), ctx)
+
+
+def lbm_slab_halo_unpack(ctx, side, src):
+    _check(lib().lbm_slab_halo_unpack(ctx, int(side), src.data_ptr() if hasattr(src, "data_ptr") else src), ctx)
+
+
+def lbm_slab_info(ctx):
+    """(a_begin, a_end, ghosts_below, ghosts_above)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().lbm_slab_info(ctx, *[ctypes.byref(x) for x in v]), ctx)
+    return tuple(x.value for x in v)
+
+
+def lbm_set_fp16_scale(ctx, scale):
+    _check(lib().lbm_set_fp16_scale(ctx, float(scale)), ctx)
+
+
 def _bcheck(rc, b):
     if rc != LBM_OK:
         raise LbmError(rc, lib().lbm_batch_last_error(b).decode())
@@ -325,7 +375,7 @@ def lbm_batch_destroy(b):
 # ------------------------------------------------------------ convenience
 def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
             T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0, kernel=LBM_KERNEL_AUTO,
-            tma_stages=0, mu=0.0, include_sigma=False, overlap_steps=-1):
+            tma_stages=0, mu=0.0, include_sigma=False, overlap_steps=-1, storage_probe=0):
     o = lbm_default_options()
     o.precision = precision
     o.force_order = force_order
@@ -341,6 +391,7 @@ def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0
     o.tma_stages = tma_stages
     o.mu = mu
     o.overlap_steps = int(overlap_steps)
+    o.storage_probe = int(storage_probe)
     return o
 
 
@@ -352,7 +403,7 @@ class Sim:
     """
 
     def __init__(self, w, stream=None, block_x=0, graph_steps=0, precision=None,
-                 kernel=LBM_KERNEL_AUTO, tma_stages=0, overlap_steps=-1):
+                 kernel=LBM_KERNEL_AUTO, tma_stages=0, overlap_steps=-1, storage_probe=0):
         self.w = w
         self.lat = w["lattice"]
         self.D, self.Q, self.c, self.e, self.wts = lbm_lattice_info(self.lat)
@@ -362,7 +413,7 @@ class Sim:
         self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
                            w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
                            block_x, graph_steps, kernel, tma_stages, w.get("mu", 0.0),
-                           w.get("include_sigma", False), overlap_steps)
+                           w.get("include_sigma", False), overlap_steps, storage_probe)
         g = w.get("g")
         self._gfield = g
         self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)

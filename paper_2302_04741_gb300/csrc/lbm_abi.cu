@@ -67,43 +67,10 @@ void info_of(int* D, int* Q, double* c, int* e, double* w) {
   }
 }
 
-// Equilibrium deviation f0_i(1, 0, T) - w_i = w_i A0(|xi_i|^2) of a wall at
-// rest (u = 0), the rest-frame value of the Hermite-expanded equilibrium.
-template <class L>
-void wall_equilibrium(double T, double* fwd, double* fw) {
-  const double th = T - 1.0;
-  const int D = L::D;
-  for (int i = 0; i < L::Q; ++i) {
-    const double e2 = L::e[i][0] * L::e[i][0] + L::e[i][1] * L::e[i][1] + L::e[i][2] * L::e[i][2];
-    const double X2 = L::c2 * e2;
-    double a0 = 0.5 * th * (X2 - D);
-    if (L::NEQ >= 4) a0 += (3.0 * th * th * (X2 * X2 - 2.0 * (D + 2) * X2 + D * (D + 2))) / 24.0;
-    fwd[i] = L::w[i] * a0;
-    fw[i] = L::w[i] + fwd[i];
-  }
-}
-
 // The FP16 codec factors of the context's lattice for its current scale.
 void fp16_factors(lbm_ctx* c) {
   if (c->lat == LBM_D2Q37) lbm::set_fp16_factors<lbm::D2Q37>(c->p);
   else lbm::set_fp16_factors<lbm::D3Q39>(c->p);
-}
-
-template <class L>
-void wall_tables(StepParams& p, double T_lo, double T_hi) {
-  const int A = L::D - 1;
-  for (int side = 0; side < 2; ++side) {
-    wall_equilibrium<L>(side == 0 ? T_lo : T_hi, p.fwd[side], p.fw[side]);
-    double sfwd = 0.0, sfw = 0.0;
-    for (int i = 0; i < L::Q; ++i) {
-      const int eA = L::e[i][A];
-      const int cnt = side == 0 ? (eA > 0 ? eA : 0) : (eA < 0 ? -eA : 0);  // slots per column
-      sfwd += cnt * p.fwd[side][i];
-      sfw += cnt * p.fw[side][i];
-    }
-    p.wallA[side] = -sfwd;
-    p.wall_inv_den[side] = 1.0 / sfw;
-  }
 }
 
 bool is_device_ptr(const void* ptr) {
@@ -381,8 +348,16 @@ int lbm_lattice_info(lbm_lattice lat, int* D, int* Q, double* c, int* e, double*
   return LBM_OK;
 }
 
-int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gfield* g,
-               const lbm_options* opt, lbm_ctx** out) {
+}  // extern "C"
+
+namespace {
+// A slab of the last axis (lbm_create_slab): global layers [a_begin, a_end).
+struct SlabSpec {
+  int a_begin, a_end;
+};
+
+int create_impl(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gfield* g,
+                const lbm_options* opt, const SlabSpec* slab, lbm_ctx** out) {
   if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
   *out = nullptr;
   const lbm::LatticeOps* ops = ops_of(lat);
@@ -437,6 +412,14 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   if (!(o.mu >= 0.0) || !std::isfinite(o.mu)) return fail(nullptr, LBM_EINVAL, "mu must be >= 0");
   if (o.overlap_steps < -1 || o.overlap_steps > 1)
     return fail(nullptr, LBM_EINVAL, "overlap_steps must be -1, 0 or 1 (got %d)", o.overlap_steps);
+  if (o.storage_probe != 0) {
+    if (o.storage_probe != LBM_FP32_SHIFTED && o.storage_probe != LBM_FP16_SCALED)
+      return fail(nullptr, LBM_EINVAL, "storage_probe must be 0, LBM_FP32_SHIFTED or LBM_FP16_SCALED");
+    if (o.precision != LBM_FP64)
+      return fail(nullptr, LBM_EINVAL, "storage_probe needs LBM_FP64 storage");
+    if (o.kernel != LBM_KERNEL_AUTO && o.kernel != LBM_KERNEL_PLAIN)
+      return fail(nullptr, LBM_EINVAL, "storage_probe runs in the plain step kernel only");
+  }
   if (o.tma_stages != 0 && (o.tma_stages < 2 || o.tma_stages > 8))
     return fail(nullptr, LBM_EINVAL, "tma_stages must be 0 or 2..8 (got %d)", o.tma_stages);
   lbm_gfield gf{};
@@ -446,10 +429,36 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   if (gf.kind == LBM_G_SINE && (gf.wave_axis < 0 || gf.wave_axis >= D))
     return fail(nullptr, LBM_EINVAL, "bad wave_axis %d", gf.wave_axis);
   if (gf.kind == LBM_G_FIELD && !gf.field) return fail(nullptr, LBM_EINVAL, "force field is NULL");
+  // slab: the buffer holds the slab's layers plus 3 ghost layers on each side
+  // that is not a wall (the pull reaches 3 layers along every axis)
+  const int A = D - 1, nAg = n[A];
+  int gb = 0, ga = 0, na = nAg, a_begin = 0;
+  if (slab) {
+    if (slab->a_begin < 0 || slab->a_end > nAg || slab->a_end - slab->a_begin < 3)
+      return fail(nullptr, LBM_EINVAL, "slab layers [%d, %d) must lie in [0, %d) and number at least 3",
+                  slab->a_begin, slab->a_end, nAg);
+    if (o.kernel != LBM_KERNEL_AUTO && o.kernel != LBM_KERNEL_PLAIN)
+      return fail(nullptr, LBM_EINVAL, "slabs run in the plain step kernel");
+    if (o.graph_steps != 0)
+      return fail(nullptr, LBM_EINVAL, "slabs are stepped one step at a time (graph_steps must be 0)");
+    if (o.storage_probe != 0) return fail(nullptr, LBM_EINVAL, "slabs take no storage probe");
+    const bool periodic = wall == lbm::W_NONE;
+    gb = (periodic || slab->a_begin > 0) ? 3 : 0;
+    ga = (periodic || slab->a_end < nAg) ? 3 : 0;
+    na = slab->a_end - slab->a_begin;
+    a_begin = slab->a_begin;
+  }
+  const int nb = na + gb + ga;  // buffer layers along the last axis
+  const int bny = D == 2 ? nb : ny, bnz = D == 3 ? nb : nz;
+  const long long S = D == 2 ? (long long)nx : (long long)nx * ny;  // sites per layer
+  const long long NB = S * nb;
+  if (NB >= (1LL << 31)) return fail(nullptr, LBM_EINVAL, "slab buffer has %lld >= 2^31 sites", NB);
 
   lbm_ctx* c = new (std::nothrow) lbm_ctx();
   if (!c) return fail(nullptr, LBM_ENOMEM, "out of host memory");
-  c->lat = lat; c->D = D; c->Q = ops->Q; c->nx = nx; c->ny = ny; c->nz = nz; c->N = (int)N;
+  c->lat = lat; c->D = D; c->Q = ops->Q; c->nx = nx; c->ny = bny; c->nz = bnz; c->N = (int)NB;
+  c->slab = slab != nullptr;
+  c->a_begin = a_begin; c->a_end = a_begin + na; c->n_axis = nAg; c->gb = gb; c->ga = ga;
   c->tau = tau; c->opt = o; c->ops = ops;
   c->fo = o.include_sigma && o.force_order == 2 ? 3 : o.force_order;
   // measured on GB300: +1.3 to +2 % (graphs) and +7 % (plain launches) on
@@ -474,7 +483,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
     }
     c->own_stream = true;
   }
-  const size_t fbytes = (size_t)c->Q * N * c->elem;
+  const size_t fbytes = (size_t)c->Q * NB * c->elem;
   for (int k = 0; k < 2; ++k) {
     if (cudaMalloc(&c->f[k], fbytes) != cudaSuccess) {
       cudaGetLastError();
@@ -485,7 +494,9 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   }
   // parameters
   StepParams& p = c->p;
-  p.nx = nx; p.ny = ny; p.nz = nz; p.N = (int)N; p.wall = wall;
+  p.nx = nx; p.ny = bny; p.nz = bnz; p.N = (int)NB; p.wall = wall;
+  p.a0 = gb;
+  p.na = na;
   p.omega = 1.0 / tau;
   p.gkind = gf.kind; p.gaxis = gf.wave_axis;
   for (int a = 0; a < 3; ++a) p.g0[a] = a < D ? gf.g0[a] : 0.0;
@@ -497,30 +508,40 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   p.h_scale = 1.0f; p.h_inv_scale = 1.0f;
   fp16_factors(c);
   p.l2_evict_first = lbm::l2_evict_first_for(2 * fbytes, c->device);
+  p.storage_probe = o.storage_probe;
   if (wall != lbm::W_NONE) {
-    if (lat == LBM_D2Q37) wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
-    else wall_tables<lbm::D3Q39>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
+    if (lat == LBM_D2Q37) lbm::wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
+    else lbm::wall_tables<lbm::D3Q39>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
   }
+  // table length along the wave axis: the buffer's layers on a slab's last axis
+  const int bn[3] = {nx, bny, bnz};
   if (gf.kind == LBM_G_SINE) {
-    const int na = n[gf.wave_axis];
-    double* h = (double*)std::malloc(sizeof(double) * na);
+    const int nw = n[gf.wave_axis], nt = bn[gf.wave_axis];
+    const int off = gf.wave_axis == A ? a_begin - gb : 0;  // global index of table entry 0
+    double* h = (double*)std::malloc(sizeof(double) * nt);
     if (!h) { fail(c, LBM_ENOMEM, "out of host memory"); return bail(LBM_ENOMEM); }
-    for (int k = 0; k < na; ++k) h[k] = std::sin(2.0 * M_PI * k / na);
-    cudaError_t e = cudaMalloc(&c->gtab, sizeof(double) * na);
-    if (e == cudaSuccess) e = cudaMemcpy(c->gtab, h, sizeof(double) * na, cudaMemcpyHostToDevice);
+    for (int k = 0; k < nt; ++k) h[k] = std::sin(2.0 * M_PI * (((off + k) % nw + nw) % nw) / nw);
+    cudaError_t e = cudaMalloc(&c->gtab, sizeof(double) * nt);
+    if (e == cudaSuccess) e = cudaMemcpy(c->gtab, h, sizeof(double) * nt, cudaMemcpyHostToDevice);
     std::free(h);
     if (e != cudaSuccess) { cudaGetLastError(); fail(c, LBM_ECUDA, "force table upload failed"); return bail(LBM_ECUDA); }
-    c->bytes += sizeof(double) * na;
+    c->bytes += sizeof(double) * nt;
   } else if (gf.kind == LBM_G_FIELD) {
-    const size_t gb = sizeof(double) * D * N;
-    cudaError_t e = cudaMalloc(&c->gtab, gb);
-    if (e == cudaSuccess) e = cudaMemcpy(c->gtab, gf.field, gb, cudaMemcpyDefault);
+    // the caller's field covers the grid (a slab's own layers); the buffer's
+    // ghost layers are never read and stay zero
+    const size_t gbytes = sizeof(double) * D * NB;
+    const size_t nuser = (size_t)S * na;
+    cudaError_t e = cudaMalloc(&c->gtab, gbytes);
+    if (e == cudaSuccess) e = cudaMemset(c->gtab, 0, gbytes);
+    for (int k = 0; k < D && e == cudaSuccess; ++k)
+      e = cudaMemcpy(c->gtab + (size_t)k * NB + (size_t)gb * S, gf.field + (size_t)k * nuser,
+                     sizeof(double) * nuser, cudaMemcpyDefault);
     if (e != cudaSuccess) { cudaGetLastError(); fail(c, LBM_ECUDA, "force field upload failed"); return bail(LBM_ECUDA); }
-    c->bytes += gb;
+    c->bytes += gbytes;
   }
   p.gtab = c->gtab;
   if (c->gtab) {  // float copy of the force table for the float kernels
-    const size_t cnt = gf.kind == LBM_G_SINE ? (size_t)n[gf.wave_axis] : (size_t)D * N;
+    const size_t cnt = gf.kind == LBM_G_SINE ? (size_t)bn[gf.wave_axis] : (size_t)D * NB;
     float* ft = nullptr;
     double* h = (double*)std::malloc(sizeof(double) * cnt);
     float* hf = (float*)std::malloc(sizeof(float) * cnt);
@@ -547,7 +568,7 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   {
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
-    const long long tiles = (long long)((nx + 127) / 128) * ny * nz;
+    const long long tiles = (long long)((nx + 127) / 128) * (D == 2 ? na : (long long)ny * na);
     c->nblk_cons = (int)std::min<long long>(tiles, (long long)LBM_CONSERVED_BLOCKS * (nsm > 0 ? nsm : 1));
   }
   const size_t pb = sizeof(double) * lbm::CONS_SLOT * c->nblk_cons;
@@ -580,14 +601,139 @@ int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gf
   return LBM_OK;
 }
 
+// ---- halo exchange of slabs
+// One halo message: the planes (a layer of one population) that the
+// neighbour's own sites pull from its ghost layers.  A site pulls
+// f*_i(x - e_i), so a neighbour above reads population i with e_iA > 0 from
+// its ghost layer g (0 = farthest, 2 = adjacent to its own layers) when
+// e_iA >= 3 - g, and a neighbour below reads population i with e_iA < 0 from
+// its ghost layer h (0 = adjacent) when -e_iA >= h + 1.
+constexpr int kMaxHaloPlanes = 32;
+struct HaloPlanes {
+  int n;
+  long long src[kMaxHaloPlanes], dst[kMaxHaloPlanes];  // element offsets of each plane
+};
+
+// dir 1: the message to the neighbour above (its lower ghosts), dir 0: to the
+// neighbour below (its upper ghosts); (g, i) in message order.
+int halo_list(const lbm_ctx* c, int dir, int* layer, int* pop) {
+  int e[39 * 3];
+  lbm_lattice_info((lbm_lattice)c->lat, nullptr, nullptr, nullptr, e, nullptr);
+  const int A = c->D - 1;
+  int n = 0;
+  for (int g = 0; g < 3; ++g)
+    for (int i = 0; i < c->Q; ++i) {
+      const int eA = e[3 * i + A];
+      const bool take = dir == 1 ? eA >= 3 - g : -eA >= g + 1;
+      if (take) {
+        layer[n] = g;
+        pop[n] = i;
+        ++n;
+      }
+    }
+  return n;
+}
+
+size_t layer_sites(const lbm_ctx* c) { return (size_t)(c->D == 2 ? c->nx : c->nx * c->ny); }
+
+// Plane offsets for sending dir's message out of `from` (its own layers) and
+// writing it into `to`'s ghost layers; either side may be a contiguous
+// message instead (from == nullptr: source is the message, to == nullptr:
+// destination is the message).
+HaloPlanes halo_planes(const lbm_ctx* ref, int dir, const lbm_ctx* from, const lbm_ctx* to) {
+  int layer[kMaxHaloPlanes * 2], pop[kMaxHaloPlanes * 2];
+  HaloPlanes hp{};
+  hp.n = halo_list(ref, dir, layer, pop);
+  const long long S = (long long)layer_sites(ref);
+  for (int k = 0; k < hp.n; ++k) {
+    const int g = layer[k], i = pop[k];
+    // source layer in `from`: the top three own layers (dir 1) or the bottom three (dir 0)
+    hp.src[k] = from ? (long long)i * from->N +
+                           (long long)(dir == 1 ? from->gb + (from->a_end - from->a_begin) - 3 + g : from->gb + g) * S
+                     : (long long)k * S;
+    // destination ghost layer in `to`: below its own layers (dir 1) or above (dir 0)
+    hp.dst[k] = to ? (long long)i * to->N +
+                         (long long)(dir == 1 ? g : to->gb + (to->a_end - to->a_begin) + g) * S
+                   : (long long)k * S;
+  }
+  return hp;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_halo_copy(const T* __restrict__ src, T* __restrict__ dst,
+                                                   const HaloPlanes hp, long long S) {
+  const int k = blockIdx.y;
+  const T* s = src + hp.src[k];
+  T* d = dst + hp.dst[k];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < S; j += (long long)gridDim.x * blockDim.x)
+    d[j] = s[j];
+}
+
+cudaError_t launch_halo(const void* src, void* dst, const HaloPlanes& hp, size_t S, size_t elem,
+                        cudaStream_t st) {
+  if (hp.n == 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min<size_t>((S + 255) / 256, 1024), (unsigned)hp.n);
+  if (elem == 8) k_halo_copy<unsigned long long><<<grid, 256, 0, st>>>((const unsigned long long*)src, (unsigned long long*)dst, hp, (long long)S);
+  else if (elem == 4) k_halo_copy<unsigned><<<grid, 256, 0, st>>>((const unsigned*)src, (unsigned*)dst, hp, (long long)S);
+  else k_halo_copy<unsigned short><<<grid, 256, 0, st>>>((const unsigned short*)src, (unsigned short*)dst, hp, (long long)S);
+  return cudaGetLastError();
+}
+
+// v <- half(float(v) * factor) over n halves (factor a power of two).
+__global__ void k_rescale_half(unsigned short* __restrict__ f, size_t n, float factor) {
+  for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x)
+    f[j] = __half_as_ushort(__float2half_rn(__half2float(__ushort_as_half(f[j])) * factor));
+}
+
+// Sites of the caller's arrays: the whole grid, or a slab's own layers.
+size_t user_sites(const lbm_ctx* c) {
+  return c->slab ? (size_t)(c->D == 2 ? c->nx : c->nx * c->ny) * (c->a_end - c->a_begin) : (size_t)c->N;
+}
+// Offset of a slab's first own site in its buffer (0 without a slab).
+size_t user_offset(const lbm_ctx* c) {
+  return c->slab ? (size_t)(c->D == 2 ? c->nx : c->nx * c->ny) * c->gb : 0;
+}
+// rows x n doubles between a caller array (row stride n_user) and a buffer
+// laid out like the context (row stride N, own sites from user_offset)
+cudaError_t copy_rows(lbm_ctx* c, double* dst, const double* src, int rows, bool to_user) {
+  const size_t nu = user_sites(c), nb = (size_t)c->N, off = user_offset(c);
+  if (to_user)
+    return cudaMemcpy2DAsync(dst, nu * sizeof(double), src + off, nb * sizeof(double), nu * sizeof(double), rows,
+                             cudaMemcpyDefault, c->stream);
+  return cudaMemcpy2DAsync(dst + off, nb * sizeof(double), src, nu * sizeof(double), nu * sizeof(double), rows,
+                           cudaMemcpyDefault, c->stream);
+}
+}  // namespace
+
+extern "C" {
+
+int lbm_create(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_gfield* g,
+               const lbm_options* opt, lbm_ctx** out) {
+  return create_impl(lat, nx, ny, nz, tau, g, opt, nullptr, out);
+}
+
+int lbm_create_slab(lbm_lattice lat, int nx, int ny, int nz, int a_begin, int a_end, double tau,
+                    const lbm_gfield* g, const lbm_options* opt, lbm_ctx** out) {
+  const SlabSpec s{a_begin, a_end};
+  return create_impl(lat, nx, ny, nz, tau, g, opt, &s, out);
+}
+
 int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
   if (!rho || !u || !T) return fail(c, LBM_EINVAL, "rho, u and T are required");
   LBM_CUDA(c, cudaSetDevice(c->device));
   const size_t N = (size_t)c->N;
   const double *drho = device_view(rho), *du = device_view(u), *dT = device_view(T);
-  const bool dev = drho && du && dT;
-  if (!dev) {
+  const bool dev = drho && du && dT && !c->slab;
+  if (c->slab) {
+    int rc = ensure_tmp(c);
+    if (rc) return rc;
+    double* t = c->tmp;
+    LBM_CUDA(c, copy_rows(c, t, rho, 1, false));
+    LBM_CUDA(c, copy_rows(c, t + N, u, c->D, false));
+    LBM_CUDA(c, copy_rows(c, t + (1 + c->D) * N, T, 1, false));
+    drho = t; du = t + N; dT = t + (1 + c->D) * N;
+  } else if (!dev) {
     int rc = ensure_tmp(c);
     if (rc) return rc;
     double* t = c->tmp;
@@ -597,7 +743,7 @@ int lbm_init(lbm_ctx* c, const double* rho, const double* u, const double* T) {
     drho = t; du = t + N; dT = t + (1 + c->D) * N;
   }
   c->cur = 0;
-  if (c->opt.precision == LBM_FP16_SCALED) {
+  if (c->opt.precision == LBM_FP16_SCALED || c->opt.storage_probe == LBM_FP16_SCALED) {
     LBM_CUDA(c, cudaMemsetAsync(c->dmax, 0, sizeof(unsigned), c->stream));
     LBM_CUDA(c, c->ops->init(c->opt.precision, 0, drho, du, dT, c->f[0], c->dmax, c->opt.force_order, c->p, c->stream));
     unsigned bits = 0;
@@ -634,6 +780,7 @@ int lbm_set_solid(lbm_ctx* c, const unsigned char* solid, const double* T_wall) 
   if (c->initialised) return fail(c, LBM_ESTATE, "lbm_set_solid must precede lbm_init");
   if (c->batch) return fail(c, LBM_ESTATE, "ctx is in a batch");
   if (c->p.wall != lbm::W_NONE) return fail(c, LBM_EINVAL, "solid sites need all axes periodic");
+  if (c->slab) return fail(c, LBM_EINVAL, "solid sites are not supported on slabs");
   if (c->opt.precision == LBM_FP16_SCALED)
     return fail(c, LBM_EINVAL, "solid sites run with FP64 or FP32-shifted storage");
   if (c->use_tma || c->use_async || c->use_wave)
@@ -712,16 +859,19 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* T, double* q) {
   bool staged[4];
   double* t = c->tmp;
   for (int k = 0; k < 4; ++k) {
-    dst[k] = outs[k] ? device_view(outs[k]) : nullptr;
+    dst[k] = outs[k] && !c->slab ? device_view(outs[k]) : nullptr;
     staged[k] = outs[k] && !dst[k];
     if (staged[k]) dst[k] = t;
     t += cnt[k];
   }
   LBM_CUDA(c, c->ops->moments(c->opt.precision, c->f[c->cur], dst[0], dst[1], dst[2], dst[3],
                               c->fo, c->p, c->stream));
+  const int rows[4] = {1, c->D, 1, c->D};
   for (int k = 0; k < 4; ++k)
-    if (staged[k])
-      LBM_CUDA(c, cudaMemcpyAsync(outs[k], dst[k], cnt[k] * sizeof(double), cudaMemcpyDefault, c->stream));
+    if (staged[k]) {
+      if (c->slab) LBM_CUDA(c, copy_rows(c, outs[k], dst[k], rows[k], true));
+      else LBM_CUDA(c, cudaMemcpyAsync(outs[k], dst[k], cnt[k] * sizeof(double), cudaMemcpyDefault, c->stream));
+    }
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
@@ -759,13 +909,15 @@ int lbm_get_populations(lbm_ctx* c, double* out) {
   if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_get_populations before lbm_init");
   LBM_CUDA(c, cudaSetDevice(c->device));
   const size_t n = (size_t)c->Q * c->N;
-  const bool dev = is_device_ptr(out);
+  const bool dev = is_device_ptr(out) && !c->slab;
   double* dst = out;
   if (!dev) {
     LBM_CUDA(c, cudaMallocAsync(&dst, n * sizeof(double), c->stream));
   }
   cudaError_t e = c->ops->pulled(c->opt.precision, c->f[c->cur], dst, c->p, c->stream);
-  if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && !dev)
+    e = c->slab ? copy_rows(c, out, dst, c->Q, true)
+                : cudaMemcpyAsync(out, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (!dev) cudaFreeAsync(dst, c->stream);
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "get_populations failed: %s", cudaGetErrorString(e));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -775,15 +927,19 @@ int lbm_get_populations(lbm_ctx* c, double* out) {
 static int state_io(lbm_ctx* c, double* io, int dir) {
   LBM_CUDA(c, cudaSetDevice(c->device));
   const size_t n = (size_t)c->Q * c->N;
-  const bool dev = is_device_ptr(io);
+  const bool dev = is_device_ptr(io) && !c->slab;
   double* d = io;
   if (!dev) {
     LBM_CUDA(c, cudaMallocAsync(&d, n * sizeof(double), c->stream));
-    if (dir == 1) LBM_CUDA(c, cudaMemcpyAsync(d, io, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (dir == 1) {
+      if (c->slab) LBM_CUDA(c, copy_rows(c, d, io, c->Q, false));
+      else LBM_CUDA(c, cudaMemcpyAsync(d, io, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
   }
   cudaError_t e = c->ops->state(c->opt.precision, dir, c->f[c->cur], d, c->p, c->stream);
   if (e == cudaSuccess && !dev && dir == 0)
-    e = cudaMemcpyAsync(io, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    e = c->slab ? copy_rows(c, io, d, c->Q, true)
+                : cudaMemcpyAsync(io, d, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (!dev) cudaFreeAsync(d, c->stream);
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "state transfer failed: %s", cudaGetErrorString(e));
   LBM_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -894,6 +1050,92 @@ int lbm_load(lbm_ctx* c, const char* path) {
   fp16_factors(c);
   c->steps = hd.steps;
   c->initialised = true;
+  lbm::batch_mark_dirty(c->batch);
+  return LBM_OK;
+}
+
+size_t lbm_slab_halo_bytes(const lbm_ctx* c) {
+  if (!c || !c->slab) return 0;
+  int layer[kMaxHaloPlanes * 2], pop[kMaxHaloPlanes * 2];
+  return (size_t)halo_list(c, 1, layer, pop) * layer_sites(c) * c->elem;
+}
+
+int lbm_slab_halo_pack(lbm_ctx* c, int side, void* dst) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!c->slab) return fail(c, LBM_EINVAL, "ctx is not a slab");
+  if (side != 0 && side != 1) return fail(c, LBM_EINVAL, "side must be 0 (below) or 1 (above)");
+  if ((side == 0 ? c->gb : c->ga) == 0) return fail(c, LBM_EINVAL, "no neighbour on that side (a wall)");
+  if (!dst || !is_device_ptr(dst)) return fail(c, LBM_EINVAL, "dst must be device memory");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_slab_halo_pack before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const HaloPlanes hp = halo_planes(c, side, c, nullptr);
+  LBM_CUDA(c, launch_halo(c->f[c->cur], dst, hp, layer_sites(c), c->elem, c->stream));
+  return LBM_OK;
+}
+
+int lbm_slab_halo_unpack(lbm_ctx* c, int side, const void* src) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!c->slab) return fail(c, LBM_EINVAL, "ctx is not a slab");
+  if (side != 0 && side != 1) return fail(c, LBM_EINVAL, "side must be 0 (below) or 1 (above)");
+  if ((side == 0 ? c->gb : c->ga) == 0) return fail(c, LBM_EINVAL, "no neighbour on that side (a wall)");
+  if (!src || !is_device_ptr(src)) return fail(c, LBM_EINVAL, "src must be device memory");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_slab_halo_unpack before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  // the message from below is the lower neighbour's upward message (dir 1)
+  const HaloPlanes hp = halo_planes(c, side == 0 ? 1 : 0, nullptr, c);
+  LBM_CUDA(c, launch_halo(src, c->f[c->cur], hp, layer_sites(c), c->elem, c->stream));
+  return LBM_OK;
+}
+
+int lbm_slab_exchange(lbm_ctx* lo, lbm_ctx* hi) {
+  if (!lo || !hi) return fail(nullptr, LBM_EINVAL, "both slabs are required");
+  if (!lo->slab || !hi->slab) return fail(lo, LBM_EINVAL, "both contexts must be slabs");
+  if (lo->lat != hi->lat || lo->opt.precision != hi->opt.precision || lo->nx != hi->nx ||
+      (lo->D == 3 && lo->ny != hi->ny) || lo->n_axis != hi->n_axis)
+    return fail(lo, LBM_EINVAL, "slabs of different grids");
+  const bool adjacent = lo->a_end == hi->a_begin || (lo->a_end == lo->n_axis && hi->a_begin == 0);
+  if (!adjacent || lo->ga == 0 || hi->gb == 0)
+    return fail(lo, LBM_EINVAL, "hi must follow lo along the last axis (periodic wrap included)");
+  if (!lo->initialised || !hi->initialised) return fail(lo, LBM_ESTATE, "lbm_slab_exchange before lbm_init");
+  if (lo->device != hi->device) return fail(lo, LBM_EINVAL, "slabs on different devices: use pack / unpack");
+  if (lo->opt.precision == LBM_FP16_SCALED && lo->p.h_scale != hi->p.h_scale)
+    return fail(lo, LBM_EINVAL, "FP16 slabs need one scale (lbm_set_fp16_scale)");
+  LBM_CUDA(lo, cudaSetDevice(lo->device));
+  const size_t S = layer_sites(lo);
+  HaloPlanes up = halo_planes(lo, 1, lo, hi), down = halo_planes(lo, 0, hi, lo);
+  LBM_CUDA(lo, launch_halo(lo->f[lo->cur], hi->f[hi->cur], up, S, lo->elem, lo->stream));
+  LBM_CUDA(lo, launch_halo(hi->f[hi->cur], lo->f[lo->cur], down, S, lo->elem, lo->stream));
+  return LBM_OK;
+}
+
+int lbm_slab_info(const lbm_ctx* c, int* a_begin, int* a_end, int* ghosts_below, int* ghosts_above) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (a_begin) *a_begin = c->slab ? c->a_begin : 0;
+  if (a_end) *a_end = c->slab ? c->a_end : (c->D == 2 ? c->ny : c->nz);
+  if (ghosts_below) *ghosts_below = c->gb;
+  if (ghosts_above) *ghosts_above = c->ga;
+  return LBM_OK;
+}
+
+int lbm_set_fp16_scale(lbm_ctx* c, double scale) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (c->opt.precision != LBM_FP16_SCALED) return fail(c, LBM_EINVAL, "ctx does not store FP16");
+  int ex = 0;
+  if (!(scale > 0.0) || !std::isfinite(scale) || std::frexp(scale, &ex) != 0.5 || ex < -60 || ex > 62)
+    return fail(c, LBM_EINVAL, "scale must be a power of two in [2^-60, 2^60]");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_set_fp16_scale before lbm_init");
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  const float factor = (float)(scale / (double)c->p.h_scale);
+  if (factor != 1.0f) {
+    const size_t n = (size_t)c->Q * c->N;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+    k_rescale_half<<<blocks, 256, 0, c->stream>>>((unsigned short*)c->f[c->cur], n, factor);
+    LBM_CUDA(c, cudaGetLastError());
+    drop_graphs(c);
+  }
+  c->p.h_scale = (float)scale;
+  c->p.h_inv_scale = (float)(1.0 / scale);
+  fp16_factors(c);
   lbm::batch_mark_dirty(c->batch);
   return LBM_OK;
 }

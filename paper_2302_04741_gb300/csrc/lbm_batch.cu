@@ -216,6 +216,7 @@ int lbm_batch_add(lbm_batch* b, lbm_ctx* c) {
   if (c->lat != b->lat || c->opt.precision != b->precision || c->fo != b->force_order)
     return bfail(b, LBM_EINVAL, "ctx lattice / precision / force order differ from the batch");
   if (c->solid) return bfail(b, LBM_EINVAL, "ctx has solid sites (plain step kernel only)");
+  if (c->slab) return bfail(b, LBM_EINVAL, "ctx is a slab (stepped with halo exchanges, not in batches)");
   if (c->stream != b->stream) return bfail(b, LBM_EINVAL, "ctx must use the batch's stream");
   if (c->device != b->device) return bfail(b, LBM_EINVAL, "ctx lives on another device");
   if ((int)b->members.size() >= b->cap) return bfail(b, LBM_ENOMEM, "batch is full (%d)", b->cap);

@@ -69,6 +69,12 @@ struct lbm_ctx {
   int wave_grid = 0;
   unsigned* wave_sync = nullptr;  // item counter + per-line done counts
   lbm_batch* batch = nullptr;  // batch this context is a member of
+  // slab of a grid split along its last axis (lbm_create_slab): the context
+  // holds global layers [a_begin, a_end) of that axis after gb ghost layers
+  // and before ga ghost layers (3 each, or 0 at a wall); p.a0 = gb and
+  // p.na = a_end - a_begin select the layers the kernels step
+  bool slab = false;
+  int a_begin = 0, a_end = 0, n_axis = 0, gb = 0, ga = 0;
   std::string err;
 };
 

@@ -60,6 +60,11 @@ struct StepParams {
   const double* wall_th;
   const float* wall_th_f;
   int l2_evict_first;  // 1: population loads are evict-first in L2 (see ld_pop_policy)
+  int storage_probe;   // FP64 codec: round stored deviations to P_FP32S / P_FP16S format (0 off)
+  // layers of the last axis the per-site kernels visit: a0 .. a0 + na - 1
+  // (the whole axis, a0 = 0 and na = n_axis, except on a slab context, whose
+  // buffer also holds the ghost layers of its neighbours)
+  int a0, na;
 };
 
 // The parameters a kernel of arithmetic type R reads.
@@ -221,6 +226,18 @@ template <> struct Codec<P_FP64> {
   __device__ __forceinline__ static T load(const T* ptr, const StepParams&) { return __ldg(ptr); }
   __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
 };
+
+// Storage probe of the FP64 codec (StepParams::storage_probe): the deviation
+// d rounded as the float codecs store it -- to float (P_FP32S), or to half of
+// d / w_i times the grid scale and back through the same float factors as
+// Codec<P_FP16S> (P_FP16S).  Exact arithmetic around it.
+template <int I>
+__device__ __forceinline__ double probe_round(double d, const StepParams& p) {
+  if (p.storage_probe == P_FP32S) return double(float(d));
+  if (p.storage_probe == P_FP16S)
+    return double(__half2float(__float2half_rn(float(d) * p.h_enc[I])) * p.h_dec[I]);
+  return d;
+}
 
 template <> struct Codec<P_FP32S> {
   using T = float;

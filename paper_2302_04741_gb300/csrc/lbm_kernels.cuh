@@ -316,7 +316,14 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   }
   // rest particle: t = s' = 0
   typename C::T* __restrict__ fo = fout + site;
-  fo[0] = C::template encode<L, 0>(fma(d[0], om1, mul_w<L, 0, R, EX>(P0[0])), p);
+  // FP64 storage probe: the stored deviation rounded as a float codec stores it
+  const bool probe = P == P_FP64 && p.storage_probe != 0;
+  {
+    R d0 = fma(d[0], om1, mul_w<L, 0, R, EX>(P0[0]));
+    if constexpr (P == P_FP64)
+      if (probe) d0 = probe_round<0>(d0, p);
+    fo[0] = C::template encode<L, 0>(d0, p);
+  }
   static_for<0, NP>([&](auto K) {
     constexpr int ip = 2 * K + 1, im = ip + 1;
     constexpr int sh = L::SH(ip);
@@ -334,8 +341,15 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
     if constexpr (FO == 3) od_in += stress_pair<L, ip, R>(st);
     const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip, R, EX>(ev_in));
     const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip, R, EX>(od_in));
-    fo[ip * N] = C::template encode<L, ip>(ev + od, p);
-    fo[im * N] = C::template encode<L, im>(ev - od, p);
+    R dp = ev + od, dm = ev - od;
+    if constexpr (P == P_FP64) {
+      if (probe) {
+        dp = probe_round<ip>(dp, p);
+        dm = probe_round<im>(dm, p);
+      }
+    }
+    fo[ip * N] = C::template encode<L, ip>(dp, p);
+    fo[im * N] = C::template encode<L, im>(dm, p);
   });
 }
 
@@ -363,7 +377,7 @@ constexpr int min_blocks() {
 // indices along that axis, so they start with the first wave instead of
 // forming the last blocks of the launch; the bulk rows follow in order.
 __device__ __forceinline__ int wall_rows_first(int b, int n, bool walls) {
-  if (!walls) return b;
+  if (!walls || n < 6) return b;
   return b < 3 ? b : (b < 6 ? n - 6 + b : b - 3);
 }
 
@@ -377,8 +391,8 @@ __global__ void __launch_bounds__(256, min_blocks<L, P>())
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
   const bool walls = p.wall != W_NONE;
-  const int y = L::D == 2 ? wall_rows_first(blockIdx.y, p.ny, walls) : (int)blockIdx.y;
-  const int z = L::D == 3 ? wall_rows_first(blockIdx.z, p.nz, walls) : (int)blockIdx.z;
+  const int y = L::D == 2 ? p.a0 + wall_rows_first(blockIdx.y, p.na, walls) : (int)blockIdx.y;
+  const int z = L::D == 3 ? p.a0 + wall_rows_first(blockIdx.z, p.na, walls) : (int)blockIdx.z;
   const int site = (z * p.ny + y) * p.nx + x;
   if constexpr (SOLID) {
     if (__ldg(p.solid + site)) return;
@@ -445,7 +459,8 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
   constexpr int Q = L::Q, D = L::D;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = D == 2 ? p.a0 + (int)blockIdx.y : (int)blockIdx.y;
+  const int z = D == 3 ? p.a0 + (int)blockIdx.z : 0;
   const int nx = p.nx, ny = p.ny, nz = p.nz;
   const int site = (z * ny + y) * nx + x;
   const size_t N = (size_t)p.N;
@@ -473,6 +488,13 @@ __global__ void __launch_bounds__(128) k_init(const double* __restrict__ rho,
   const int nA = D == 2 ? ny : nz;
   const int lineA = D == 2 ? nx : nx * ny;
   const int colbase = D == 2 ? x : (y * nx + x);
+  if constexpr (P == P_FP64) {  // storage probe: the initial state as a float codec stores it
+    if (p.storage_probe)
+      static_for<0, Q>([&](auto I) {
+        constexpr int i = I;
+        d[i] = probe_round<i>(d[i], p);
+      });
+  }
   static_for<0, Q>([&](auto I) {
     constexpr int i = I;
     constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
@@ -629,7 +651,8 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
   constexpr int Q = L::Q, D = L::D;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = D == 2 ? p.a0 + (int)blockIdx.y : (int)blockIdx.y;
+  const int z = D == 3 ? p.a0 + (int)blockIdx.z : 0;
   const int site = (z * p.ny + y) * p.nx + x;
   const size_t N = (size_t)p.N;
   if (p.solid && p.solid[site]) {  // solid sites report zeros
@@ -889,7 +912,7 @@ __global__ void __launch_bounds__(128, LBM_CONSERVED_BLOCKS) k_conserved(const t
   using R = typename Codec<P>::R;
   constexpr int Q = L::Q, D = L::D;
   const int ntx = (p.nx + 127) / 128;
-  const int ntiles = ntx * p.ny * p.nz;
+  const int ntiles = ntx * (D == 2 ? p.na : p.ny * p.na);
   const bool uniform = p.gkind == G_UNIFORM;
   RSum<R> sums[NCONS];
   unsigned count = 0u, bad = 0u;
@@ -898,8 +921,8 @@ __global__ void __launch_bounds__(128, LBM_CONSERVED_BLOCKS) k_conserved(const t
     // the wall rows, whose pull also gathers the wall sums, come first so
     // that they do not form the tail of the pass
     const int xt = t % ntx, row = t / ntx;
-    const int y = D == 2 ? wall_rows_first(row, p.ny, walls) : row % p.ny;
-    const int z = D == 3 ? wall_rows_first(row / p.ny, p.nz, walls) : 0;
+    const int y = D == 2 ? p.a0 + wall_rows_first(row, p.na, walls) : row % p.ny;
+    const int z = D == 3 ? p.a0 + wall_rows_first(row / p.ny, p.na, walls) : 0;
     const int x = xt * 128 + threadIdx.x;
     if (x >= p.nx) continue;
     const int site = (z * p.ny + y) * p.nx + x;
@@ -913,7 +936,15 @@ __global__ void __launch_bounds__(128, LBM_CONSERVED_BLOCKS) k_conserved(const t
     else if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
     else pull<L, P, R>(fin, p, x, y, z, d);
     R g[3];
-    site_force_r<D, R>(p, x, y, z, site, g);
+    if (sizeof(R) == sizeof(float) && p.gkind == G_FIELD && p.gtab_f == nullptr) {
+      // a caller's double field without a float copy (lbm_conserved_static),
+      // rounded to float as a context rounds its copy
+      g[0] = R(__ldg(p.gtab + site));
+      g[1] = R(__ldg(p.gtab + (size_t)p.N + site));
+      g[2] = D == 3 ? R(__ldg(p.gtab + 2 * (size_t)p.N + site)) : R(0);
+    } else {
+      site_force_r<D, R>(p, x, y, z, site, g);
+    }
     const RawMoments<L, R> r = raw_moments<L, R>(d);
     ++count;
     sums[0].add(r.drho);
@@ -986,10 +1017,11 @@ __global__ void __launch_bounds__(128) k_conserved_final(const double* __restric
 template <class L, int P>
 __global__ void __launch_bounds__(128) k_get_pulled(const typename Codec<P>::T* __restrict__ fin,
                                                     double* __restrict__ out, const StepParams p) {
-  constexpr int Q = L::Q;
+  constexpr int Q = L::Q, D = L::D;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int y = blockIdx.y, z = blockIdx.z;
+  const int y = D == 2 ? p.a0 + (int)blockIdx.y : (int)blockIdx.y;
+  const int z = D == 3 ? p.a0 + (int)blockIdx.z : 0;
   const int site = (z * p.ny + y) * p.nx + x;
   const size_t N = (size_t)p.N;
   if (p.solid && p.solid[site]) {
@@ -1010,10 +1042,12 @@ template <class L, int P, int DIR>
 __global__ void __launch_bounds__(128) k_state(typename Codec<P>::T* __restrict__ f,
                                                double* __restrict__ io, const StepParams p) {
   using C = Codec<P>;
-  constexpr int Q = L::Q;
+  constexpr int Q = L::Q, D = L::D;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= p.nx) return;
-  const int site = (blockIdx.z * p.ny + blockIdx.y) * p.nx + x;
+  const int y = D == 2 ? p.a0 + (int)blockIdx.y : (int)blockIdx.y;
+  const int z = D == 3 ? p.a0 + (int)blockIdx.z : 0;
+  const int site = (z * p.ny + y) * p.nx + x;
   const size_t N = (size_t)p.N;
   static_for<0, Q>([&](auto I) {
     constexpr int i = I;

@@ -49,8 +49,49 @@ struct LatticeOps {
                            unsigned* sync, int grid, cudaStream_t s);
 };
 
+// ---- wall tables (host side; shared by lbm_create and lbm_conserved_static)
+// Equilibrium deviation f0_i(1, 0, T) - w_i = w_i A0(|xi_i|^2) of a wall at
+// rest (u = 0), the rest-frame value of the Hermite-expanded equilibrium.
+template <class L>
+inline void wall_equilibrium(double T, double* fwd, double* fw) {
+  const double th = T - 1.0;
+  const int D = L::D;
+  for (int i = 0; i < L::Q; ++i) {
+    const double e2 = L::e[i][0] * L::e[i][0] + L::e[i][1] * L::e[i][1] + L::e[i][2] * L::e[i][2];
+    const double X2 = L::c2 * e2;
+    double a0 = 0.5 * th * (X2 - D);
+    if (L::NEQ >= 4) a0 += (3.0 * th * th * (X2 * X2 - 2.0 * (D + 2) * X2 + D * (D + 2))) / 24.0;
+    fwd[i] = L::w[i] * a0;
+    fw[i] = L::w[i] + fwd[i];
+  }
+}
+
+// The thermal-wall constants of StepParams for wall temperatures T_lo (at
+// x_a = -1/2) and T_hi (at x_a = n_a - 1/2) on the last axis: the wall
+// Maxwellian per side and the per-column mass balance of the diffuse wall.
+template <class L>
+inline void wall_tables(StepParams& p, double T_lo, double T_hi) {
+  const int A = L::D - 1;
+  for (int side = 0; side < 2; ++side) {
+    wall_equilibrium<L>(side == 0 ? T_lo : T_hi, p.fwd[side], p.fw[side]);
+    double sfwd = 0.0, sfw = 0.0;
+    for (int i = 0; i < L::Q; ++i) {
+      const int eA = L::e[i][A];
+      const int cnt = side == 0 ? (eA > 0 ? eA : 0) : (eA < 0 ? -eA : 0);  // slots per column
+      sfwd += cnt * p.fwd[side][i];
+      sfw += cnt * p.fw[side][i];
+    }
+    p.wallA[side] = -sfwd;
+    p.wall_inv_den[side] = 1.0 / sfw;
+  }
+}
+
+// Per-site launch: blocks of bx sites along x, one row per block, over the
+// layers a0 .. a0 + na - 1 of the last axis (StepParams::a0, na).
+template <int D>
 inline dim3 row_grid(const StepParams& p, int bx) {
-  return dim3((unsigned)((p.nx + bx - 1) / bx), (unsigned)p.ny, (unsigned)p.nz);
+  return dim3((unsigned)((p.nx + bx - 1) / bx), (unsigned)(D == 2 ? p.na : p.ny),
+              (unsigned)(D == 2 ? 1 : p.na));
 }
 
 template <class L>
@@ -63,7 +104,7 @@ struct Ops {
   static cudaError_t step(int P, int FO, const void* fin, void* fout, const StepParams& p, int bx,
                           bool overlap, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = row_grid(p, bx);
+    cfg.gridDim = row_grid<L::D>(p, bx);
     cfg.blockDim = dim3(bx);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
@@ -104,7 +145,7 @@ struct Ops {
   static cudaError_t init(int P, int mode, const double* rho, const double* u, const double* T_,
                           void* fout, unsigned* maxbits, int FO, const StepParams& p,
                           cudaStream_t s) {
-    const dim3 g = row_grid(p, 128), b(128);
+    const dim3 g = row_grid<L::D>(p, 128), b(128);
     if (mode == 0) {
       k_init<L, P_FP16S, 0><<<g, b, 0, s>>>(rho, u, T_, (T<P_FP16S>*)fout, maxbits, FO, p);
     } else if (P == P_FP64) {
@@ -119,7 +160,7 @@ struct Ops {
 
   static cudaError_t moments(int P, const void* fin, double* rho, double* u, double* T_,
                              double* q, int FO, const StepParams& p, cudaStream_t s) {
-    const dim3 g = row_grid(p, 128), b(128);
+    const dim3 g = row_grid<L::D>(p, 128), b(128);
     if (P == P_FP64) k_moments<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, rho, u, T_, q, FO, p);
     else if (P == P_FP32S) k_moments<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, rho, u, T_, q, FO, p);
     else k_moments<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, rho, u, T_, q, FO, p);
@@ -150,7 +191,7 @@ struct Ops {
 
   static cudaError_t pulled(int P, const void* fin, double* out, const StepParams& p,
                             cudaStream_t s) {
-    const dim3 g = row_grid(p, 128), b(128);
+    const dim3 g = row_grid<L::D>(p, 128), b(128);
     if (P == P_FP64) k_get_pulled<L, P_FP64><<<g, b, 0, s>>>((const T<P_FP64>*)fin, out, p);
     else if (P == P_FP32S) k_get_pulled<L, P_FP32S><<<g, b, 0, s>>>((const T<P_FP32S>*)fin, out, p);
     else k_get_pulled<L, P_FP16S><<<g, b, 0, s>>>((const T<P_FP16S>*)fin, out, p);
@@ -159,7 +200,7 @@ struct Ops {
 
   static cudaError_t state(int P, int dir, void* f, double* io, const StepParams& p,
                            cudaStream_t s) {
-    const dim3 g = row_grid(p, 128), b(128);
+    const dim3 g = row_grid<L::D>(p, 128), b(128);
 #define LBM_STATE_CASE(PP)                                                                 \
   if (P == PP) {                                                                           \
     if (dir == 0) k_state<L, PP, 0><<<g, b, 0, s>>>((T<PP>*)f, io, p);                     \

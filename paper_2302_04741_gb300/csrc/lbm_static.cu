@@ -76,12 +76,6 @@ int scratch_for_current_device(StaticScratch** out) {
   return LBM_OK;
 }
 
-int dev_of_current() {
-  int d = 0;
-  cudaGetDevice(&d);
-  return d;
-}
-
 // out[0] mass, out[1..3] momentum, out[4] energy, out[5] number of bad sites.
 __global__ void k_static_combine(const double* __restrict__ res, double* __restrict__ out) {
   if (threadIdx.x == 0) {
@@ -90,27 +84,17 @@ __global__ void k_static_combine(const double* __restrict__ res, double* __restr
   }
 }
 
-template <class L>
-void wall_params(lbm::StepParams& p, double T_lo, double T_hi) {
-  const int A = L::D - 1, D = L::D;
-  for (int side = 0; side < 2; ++side) {
-    const double th = (side == 0 ? T_lo : T_hi) - 1.0;
-    double sfwd = 0.0, sfw = 0.0;
-    for (int i = 0; i < L::Q; ++i) {
-      const double e2 = L::e[i][0] * L::e[i][0] + L::e[i][1] * L::e[i][1] + L::e[i][2] * L::e[i][2];
-      const double X2 = L::c2 * e2;
-      double a0 = 0.5 * th * (X2 - D);
-      if (L::NEQ >= 4) a0 += (3.0 * th * th * (X2 * X2 - 2.0 * (D + 2) * X2 + D * (D + 2))) / 24.0;
-      p.fwd[side][i] = L::w[i] * a0;
-      p.fw[side][i] = L::w[i] + p.fwd[side][i];
-      const int eA = L::e[i][A];
-      const int cnt = side == 0 ? (eA > 0 ? eA : 0) : (eA < 0 ? -eA : 0);
-      sfwd += cnt * p.fwd[side][i];
-      sfw += cnt * p.fw[side][i];
-    }
-    p.wallA[side] = -sfwd;
-    p.wall_inv_den[side] = 1.0 / sfw;
+// True when ptr is device (or managed) memory that kernels on device `dev`
+// can read: a host address, pageable or page-locked, or memory of another GPU
+// is refused before any launch.
+bool on_device(const void* ptr, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -141,6 +125,8 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   lbm::StepParams p;
   std::memset(&p, 0, sizeof p);
   p.nx = nx; p.ny = ny; p.nz = nz; p.N = nx * ny * nz;
+  p.a0 = 0;
+  p.na = D == 2 ? ny : nz;
   p.omega = 1.0;
   p.wall = lbm::W_NONE;
   for (int a = 0; a < D; ++a) {
@@ -151,8 +137,8 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
     p.wall = o.bc[a] == LBM_BOUNCE_BACK ? lbm::W_BOUNCE : lbm::W_THERMAL;
   }
   if (p.wall != lbm::W_NONE) {
-    if (lat == LBM_D2Q37) wall_params<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
-    else wall_params<lbm::D3Q39>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
+    if (lat == LBM_D2Q37) lbm::wall_tables<lbm::D2Q37>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
+    else lbm::wall_tables<lbm::D3Q39>(p, o.T_lo[D - 1], o.T_hi[D - 1]);
   }
   p.gkind = lbm::G_UNIFORM;
   if (g) {
@@ -161,7 +147,10 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
     } else if (g->kind == LBM_G_FIELD) {
       if (!g->field) return set_error(LBM_EINVAL, "force field is NULL");
       p.gkind = lbm::G_FIELD;
-      p.gtab = g->field;  // device pointer, D*N doubles
+      // device pointer, D*N doubles; p.gtab_f stays NULL: the conservation
+      // pass of the float codecs then reads this double field and rounds it
+      // to float, as a context's float copy of the field is rounded
+      p.gtab = g->field;
     } else {
       return set_error(LBM_EINVAL, "force kind must be UNIFORM or FIELD (a device array)");
     }
@@ -177,16 +166,31 @@ extern "C" int lbm_conserved_static(lbm_lattice lat, int nx, int ny, int nz,
   }
   if (lat == LBM_D2Q37) lbm::set_fp16_factors<lbm::D2Q37>(p);
   else lbm::set_fp16_factors<lbm::D3Q39>(p);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(LBM_EINVAL, "f and out must be device memory of the current device "
+                                 "(no CUDA device is usable)", e);
+  }
+  if (!on_device(f, dev)) return set_error(LBM_EINVAL, "f must be device memory of the current device");
+  if (!on_device(out, dev))
+    return set_error(LBM_EINVAL, "out must be device memory of the current device");
+  if (p.gkind == lbm::G_FIELD && !on_device(p.gtab, dev))
+    return set_error(LBM_EINVAL, "the force field must be device memory of the current device");
   StaticScratch* s = nullptr;
   int rc = scratch_for_current_device(&s);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)o.stream;
-  // the grid-stride pass writes one partial per block: at most one per tile
+  // the grid-stride pass writes one partial per block: at most one per tile;
+  // the same block count as a context's pass (lbm_create)
   int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_of_current());
+  e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_error(LBM_ECUDA, "cudaDeviceGetAttribute failed", e);
+  if (nsm < 1) nsm = 1;
   const long long cap = (long long)LBM_CONSERVED_BLOCKS * nsm;
   const int nblocks = (int)(tiles < cap ? tiles : cap);
-  cudaError_t e = ops->conserved(o.precision, f, s->part, s->bad, nullptr, nullptr, nullptr, p,
+  e = ops->conserved(o.precision, f, s->part, s->bad, nullptr, nullptr, nullptr, p,
                                  nblocks, st);
   if (e != cudaSuccess) return set_error(LBM_ECUDA, "conservation kernel launch failed", e);
   e = ops->conserved_final(o.precision, s->part, s->bad, nblocks, s->res, p, st);

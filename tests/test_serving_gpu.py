@@ -101,11 +101,21 @@ def test_tuned_server_config():
 def test_served_requests_match_oracle():
     """Requests of the serving trace's smallest side (32^3 D3Q39 boxes), served
     through continuous batching in FP32-shifted storage, agree with the FP64
-    oracle run on each request alone."""
-    from helpers import compare_fields, oracle_sim
+    oracle run on each request alone: rho, u, T and q within the FP32
+    tolerance (q with the floor and the codec bound of the parity tests).
+    Each box starts with a resolved shear wave (u ~ 1e-2) so that u is a
+    resolved flow rather than a g-driven drift at the storage floor."""
+    from helpers import check_fields, oracle_sim
     trace = [dict(id=k, arrival=0.01 * k, side=32, g=3e-6 * (k + 1), steps=30 + 10 * k, tau=0.7 + 0.1 * k,
                   seed=7) for k in range(3)]
     reqs = S.requests_from_trace(trace, W.FP32_SHIFTED)
+    for r in reqs:
+        s = r.workload["shape"][0]
+        z = np.arange(s ** 3) // (s * s)
+        u = np.zeros((3, s ** 3))
+        u[0] = 1e-2 * np.sin(2 * np.pi * z / s)
+        u[1] = 5e-3 * np.cos(2 * np.pi * z / s)
+        r.workload["u"] = u
     srv = S.Server(precision=W.FP32_SHIFTED, max_slots=4, tick_steps=10, graph_steps=4)
     try:
         srv.run(reqs, clock=TickClock())
@@ -114,10 +124,5 @@ def test_served_requests_match_oracle():
     for r in reqs:
         ref = oracle_sim(r.workload)
         ref.step(r.steps)
-        rho, u, T, q = ref.moments()
         got = (r.result["rho"], r.result["u"], r.result["T"], r.result["q"])
-        err = compare_fields(got, (rho, u, T, q), 1e-3)
-        assert all(err[k] <= 1e-6 for k in ("rho", "T")), (r.id, err)
-        # u is a small g-driven drift (~1e-4) on a still box: compare it in
-        # absolute terms, above the FP32 storage floor (~1e-8 after these steps)
-        assert np.max(np.abs(got[1] - u)) < 1e-7, (r.id, np.max(np.abs(got[1] - u)))
+        check_fields(got, ref, r.workload, 1e-6)
