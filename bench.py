@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS & % HBM roofline, FP32-shifted vs FP64 at stated L2 error; serving p50/p99"
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_tma.cuh", "lbm_async.cuh",
-                  "lbm_wave.cuh", "lbm_batch.cuh", "lbm_launch.cuh", "lattice_tables.cuh"]
+                  "lbm_wave.cuh", "lbm_batch.cuh", "lbm_launch.cuh", "lbm_df.cuh", "lattice_tables.cuh"]
 
 
 def parse_args():
@@ -93,20 +93,25 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def profiled_traffic(name):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+def profiled_value(name, key):
+    """A number recorded in a committed ncu summary (``key: value``), if the
+    summary was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as fh:
             text = fh.read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", text)
     s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
     if not m or not s or s.group(1) != kernel_source_sha():
         return None
     return float(m.group(1))
+
+
+def profiled_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary (current source only)."""
+    return profiled_value(name, "traffic_bytes_per_launch")
 
 
 class ClockSampler:
@@ -500,17 +505,50 @@ def run_ours(args):
                 "bytes_per_launch": bytes_per_launch, "avg_launch_us": t_launch * 1e6}
 
     extra = {}
-    # FP64 storage, same workload (the FP32/FP64 ratio of the target)
+    # FP64 storage, same workload (the FP32/FP64 ratio of the target), with
+    # the float-float step (the FP64 headline) and the IEEE double step
     if not args.no_fp64:
+        from paper_2302_04741_gb300 import peaks as PK
+        rates = PK.rates(reps=3)
         w64 = W.rayleigh_benard(nx=nx, ny=ny, precision=W.FP64, seed=2 + rank)
-        sim64 = lbm.Sim(w64, stream=stream.cuda_stream, graph_steps=args.graph_steps).init()
         K64 = max(2, min(K, 5))
-        t64, k64, _ = time_context(lbm, torch, sim64, stream, flush, K64, 1, inner)
-        v64 = N * inner * K64 / (t64 / 1e3) / 1e6
-        a64 = 2 * Q * 8 * N / (k64 / 1e3 / (K64 * inner)) / 1e9
-        extra["fp64"] = {"value": v64, "unit": "MLUPS", "roofline_frac_hbm": a64 / peak,
-                         "achieved_gbs": a64, "ratio_fp32_over_fp64": value / world / v64}
-        sim64.close()
+        runs = {}
+        for arith in (lbm.LBM_ARITH_FLOAT_PAIR, lbm.LBM_ARITH_DOUBLE):
+            sim64 = lbm.Sim(w64, stream=stream.cuda_stream, graph_steps=args.graph_steps,
+                            fp64_arith=arith).init()
+            t64, k64, _ = time_context(lbm, torch, sim64, stream, flush, K64, 1, inner)
+            sim64.close()
+            t_launch64 = k64 / 1e3 / (K64 * inner)
+            runs[arith] = (N * inner * K64 / (t64 / 1e3) / 1e6, 2 * Q * 8 * N / t_launch64 / 1e9, t_launch64)
+        prof = "k_step_fp64_rayleigh_benard_1024x512.md"
+        v_df, a_df, tl_df = runs[lbm.LBM_ARITH_FLOAT_PAIR]
+        v_ie, a_ie, tl_ie = runs[lbm.LBM_ARITH_DOUBLE]
+        # ALU roofline of the IEEE double step: its FP64 instructions per site
+        # (ncu count) at the measured DFMA / DADD rate
+        f64_ops = profiled_value(prof, "ieee_fp64_ops_per_site")
+        alu_ie = None
+        if f64_ops:
+            ach = f64_ops * N / tl_ie
+            alu_ie = {"bound": "fp64_alu", "achieved_ops": ach, "peak_ops": rates["dfma"],
+                      "frac": ach / rates["dfma"], "fp64_ops_per_site": f64_ops,
+                      "peak_source": "measured DFMA rate (peaks.py, this run)"}
+        # the float-float step is bound by instruction issue: thread
+        # instructions per site (ncu count) against 128 per SM per clock
+        inst = profiled_value(prof, "float_pair_inst_per_site")
+        alu_df = None
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        clk_hz = float((clk or {}).get("sm_mhz") or 2070.0) * 1e6
+        if inst:
+            ach = inst * N / tl_df
+            pk = 128.0 * nsm * clk_hz
+            alu_df = {"bound": "issue", "achieved_inst": ach, "peak_inst": pk, "frac": ach / pk,
+                      "inst_per_site": inst, "peak_source": "4 warp instructions per SM per clock x median SM clock"}
+        extra["fp64"] = {"value": v_df, "unit": "MLUPS", "arith": "float_pair (lbm_options.fp64_arith)",
+                         "roofline_frac_hbm": a_df / peak, "achieved_gbs": a_df, "roofline_alu": alu_df,
+                         "ratio_fp32_over_fp64": value / world / v_df,
+                         "ieee_double": {"value": v_ie, "unit": "MLUPS", "roofline_frac_hbm": a_ie / peak,
+                                         "achieved_gbs": a_ie, "roofline_alu": alu_ie},
+                         "measured_rates_tops": {k: v / 1e12 for k, v in rates.items()}}
         # accuracy of the FP32-shifted run against the FP64 run over the
         # configuration's full 20k steps, with the FP64 butterfly floor and the
         # FP32 storage floor (paper_2302_04741_gb300.accuracy)

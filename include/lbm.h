@@ -144,7 +144,20 @@ typedef struct {
                         storage precision of the named codec and exact
                         arithmetic: its distance from the plain FP64 run is
                         the codec's storage floor.  Plain step kernel only.  */
+  int fp64_arith;    /* LBM_FP64 storage: arithmetic of the step kernel.
+                        LBM_ARITH_DOUBLE (0, default): IEEE double.
+                        LBM_ARITH_FLOAT_PAIR (1): float-float (an unevaluated
+                        sum of two floats, ~48 significant bits) on the FP32
+                        pipe; populations stay doubles in memory and every
+                        other call of the context is unchanged.  On GPUs whose
+                        FP64 rate is a small fraction of the FP32 rate (GB300:
+                        1/73) the double step is bound by the FP64 units; the
+                        float-float step moves that bound.  Per population it
+                        agrees with the double step to about 1e-14.  Plain
+                        step kernel, no solid sites, no storage probe.        */
 } lbm_options;
+
+enum { LBM_ARITH_DOUBLE = 0, LBM_ARITH_FLOAT_PAIR = 1 };
 
 #define LBM_OVERLAP_MIN_SITES 131072
 

@@ -28,6 +28,7 @@ LBM_G_UNIFORM, LBM_G_SINE, LBM_G_FIELD = 0, 1, 2
 LBM_FP64, LBM_FP32_SHIFTED, LBM_FP16_SCALED = 0, 1, 2
 LBM_PERIODIC, LBM_BOUNCE_BACK, LBM_THERMAL_WALL = 0, 1, 2
 LBM_KERNEL_AUTO, LBM_KERNEL_PLAIN, LBM_KERNEL_TMA, LBM_KERNEL_PREFETCH, LBM_KERNEL_WAVE = 0, 1, 2, 3, 4
+LBM_ARITH_DOUBLE, LBM_ARITH_FLOAT_PAIR = 0, 1
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_EINVAL", -2: "LBM_ENOMEM", -3: "LBM_ECUDA",
                 -4: "LBM_EUNSTABLE", -5: "LBM_ETIMEOUT", -6: "LBM_ESTATE", -7: "LBM_EIO"}
 
@@ -44,7 +45,8 @@ class lbm_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("block_x", ctypes.c_int),
                 ("graph_steps", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("tma_stages", ctypes.c_int), ("mu", ctypes.c_double),
-                ("overlap_steps", ctypes.c_int), ("storage_probe", ctypes.c_int)]
+                ("overlap_steps", ctypes.c_int), ("storage_probe", ctypes.c_int),
+                ("fp64_arith", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -375,7 +377,7 @@ def lbm_batch_destroy(b):
 # ------------------------------------------------------------ convenience
 def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0),
             T_hi=(1.0, 1.0, 1.0), stream=None, block_x=0, graph_steps=0, kernel=LBM_KERNEL_AUTO,
-            tma_stages=0, mu=0.0, include_sigma=False, overlap_steps=-1, storage_probe=0):
+            tma_stages=0, mu=0.0, include_sigma=False, overlap_steps=-1, storage_probe=0, fp64_arith=0):
     o = lbm_default_options()
     o.precision = precision
     o.force_order = force_order
@@ -392,6 +394,7 @@ def options(precision=LBM_FP64, force_order=2, bc=(0, 0, 0), T_lo=(1.0, 1.0, 1.0
     o.mu = mu
     o.overlap_steps = int(overlap_steps)
     o.storage_probe = int(storage_probe)
+    o.fp64_arith = int(fp64_arith)
     return o
 
 
@@ -403,7 +406,7 @@ class Sim:
     """
 
     def __init__(self, w, stream=None, block_x=0, graph_steps=0, precision=None,
-                 kernel=LBM_KERNEL_AUTO, tma_stages=0, overlap_steps=-1, storage_probe=0):
+                 kernel=LBM_KERNEL_AUTO, tma_stages=0, overlap_steps=-1, storage_probe=0, fp64_arith=None):
         self.w = w
         self.lat = w["lattice"]
         self.D, self.Q, self.c, self.e, self.wts = lbm_lattice_info(self.lat)
@@ -413,7 +416,8 @@ class Sim:
         self.opt = options(prec, w.get("force_order", 2), w.get("bc", (0, 0, 0)),
                            w.get("T_lo", (1.0,) * 3), w.get("T_hi", (1.0,) * 3), stream,
                            block_x, graph_steps, kernel, tma_stages, w.get("mu", 0.0),
-                           w.get("include_sigma", False), overlap_steps, storage_probe)
+                           w.get("include_sigma", False), overlap_steps, storage_probe,
+                           w.get("fp64_arith", 0) if fp64_arith is None else fp64_arith)
         g = w.get("g")
         self._gfield = g
         self.ctx = lbm_create(self.lat, *self.shape, w["tau"], g, self.opt)

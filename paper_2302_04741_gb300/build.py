@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_gb300.so")
 SOURCES = ["lbm_d2q37.cu", "lbm_d3q39.cu", "lbm_abi.cu", "lbm_static.cu", "lbm_batch.cu"]
 HEADERS = ["lbm_device.cuh", "lbm_kernels.cuh", "lbm_launch.cuh", "lbm_tma.cuh", "lbm_batch.cuh",
-           "lbm_async.cuh", "lbm_wave.cuh", "lbm_ctx.h", "lattice_tables.cuh"]
+           "lbm_async.cuh", "lbm_wave.cuh", "lbm_df.cuh", "lbm_ctx.h", "lattice_tables.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

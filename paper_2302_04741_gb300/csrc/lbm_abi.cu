@@ -284,8 +284,8 @@ int launch_one_step(lbm_ctx* c) {
     e = c->ops->step_async(c->fo, c->f[c->cur], c->f[c->cur ^ 1], c->p, c->async_grid,
                            c->opt.block_x, c->stream);
   else
-    e = c->ops->step(c->opt.precision, c->fo, c->f[c->cur], c->f[c->cur ^ 1], c->p,
-                     c->opt.block_x, c->overlap, c->stream);
+    e = c->ops->step(c->opt.fp64_arith == LBM_ARITH_FLOAT_PAIR ? (int)lbm::P_FP64DF : c->opt.precision,
+                     c->fo, c->f[c->cur], c->f[c->cur ^ 1], c->p, c->opt.block_x, c->overlap, c->stream);
   if (e != cudaSuccess) return fail(c, LBM_ECUDA, "step launch failed: %s", cudaGetErrorString(e));
   c->cur ^= 1;
   return LBM_OK;
@@ -412,6 +412,14 @@ int create_impl(lbm_lattice lat, int nx, int ny, int nz, double tau, const lbm_g
   if (!(o.mu >= 0.0) || !std::isfinite(o.mu)) return fail(nullptr, LBM_EINVAL, "mu must be >= 0");
   if (o.overlap_steps < -1 || o.overlap_steps > 1)
     return fail(nullptr, LBM_EINVAL, "overlap_steps must be -1, 0 or 1 (got %d)", o.overlap_steps);
+  if (o.fp64_arith != LBM_ARITH_DOUBLE) {
+    if (o.fp64_arith != LBM_ARITH_FLOAT_PAIR)
+      return fail(nullptr, LBM_EINVAL, "fp64_arith must be LBM_ARITH_DOUBLE or LBM_ARITH_FLOAT_PAIR");
+    if (o.precision != LBM_FP64) return fail(nullptr, LBM_EINVAL, "fp64_arith needs LBM_FP64 storage");
+    if (o.storage_probe != 0) return fail(nullptr, LBM_EINVAL, "fp64_arith and storage_probe exclude each other");
+    if (o.kernel != LBM_KERNEL_AUTO && o.kernel != LBM_KERNEL_PLAIN)
+      return fail(nullptr, LBM_EINVAL, "fp64_arith runs in the plain step kernel only");
+  }
   if (o.storage_probe != 0) {
     if (o.storage_probe != LBM_FP32_SHIFTED && o.storage_probe != LBM_FP16_SCALED)
       return fail(nullptr, LBM_EINVAL, "storage_probe must be 0, LBM_FP32_SHIFTED or LBM_FP16_SCALED");
@@ -781,6 +789,8 @@ int lbm_set_solid(lbm_ctx* c, const unsigned char* solid, const double* T_wall) 
   if (c->batch) return fail(c, LBM_ESTATE, "ctx is in a batch");
   if (c->p.wall != lbm::W_NONE) return fail(c, LBM_EINVAL, "solid sites need all axes periodic");
   if (c->slab) return fail(c, LBM_EINVAL, "solid sites are not supported on slabs");
+  if (c->opt.fp64_arith != LBM_ARITH_DOUBLE)
+    return fail(c, LBM_EINVAL, "solid sites run with IEEE double arithmetic (fp64_arith 0)");
   if (c->opt.precision == LBM_FP16_SCALED)
     return fail(c, LBM_EINVAL, "solid sites run with FP64 or FP32-shifted storage");
   if (c->use_tma || c->use_async || c->use_wave)

@@ -14,12 +14,15 @@
 #include <type_traits>
 
 #include "lattice_tables.cuh"
+#include "lbm_df.cuh"
 
 namespace lbm {
 
 constexpr int QMAX = 39;
 
-enum Precision { P_FP64 = 0, P_FP32S = 1, P_FP16S = 2 };
+// P_FP64DF: FP64 storage with float-float arithmetic in the step kernel
+// (the other kernels of such a context run P_FP64 on the same buffers).
+enum Precision { P_FP64 = 0, P_FP32S = 1, P_FP16S = 2, P_FP64DF = 3 };
 enum Wall { W_NONE = 0, W_BOUNCE = 1, W_THERMAL = 2 };
 enum GKind { G_UNIFORM = 0, G_SINE = 1, G_FIELD = 2 };
 
@@ -87,6 +90,15 @@ struct ParamsOf<float> {
   __device__ __forceinline__ static float gtab(const StepParams& p, size_t k) { return __ldg(p.gtab_f + k); }
 };
 
+template <>
+struct ParamsOf<DF> {
+  __device__ __forceinline__ static DF wall_th(const StepParams& p, int k) { return df_split(__ldg(p.wall_th + k)); }
+  __device__ __forceinline__ static DF omega(const StepParams& p) { return df_split(p.omega); }
+  __device__ __forceinline__ static DF mu(const StepParams& p) { return df_split(p.mu); }
+  __device__ __forceinline__ static DF g0(const StepParams& p, int a) { return df_split(p.g0[a]); }
+  __device__ __forceinline__ static DF gtab(const StepParams& p, size_t k) { return df_split(__ldg(p.gtab + k)); }
+};
+
 // ---------------------------------------------------------------- helpers
 // Compile-time index usable in device code (std::integral_constant's
 // conversion operator is host-only).
@@ -149,7 +161,8 @@ __host__ __device__ constexpr F2 f2_of(double k) {
 // float-rounded constant costs): one float multiply instead of two.
 template <class R, bool EX = true>
 __device__ __forceinline__ R kmul(double k, F2 k2, R x) {
-  if constexpr (sizeof(R) == sizeof(double)) return R(k) * x;
+  if constexpr (std::is_same<R, DF>::value) return DF(k2.hi, k2.lo) * x;  // the constant's float-float split
+  else if constexpr (sizeof(R) == sizeof(double)) return R(k) * x;
   else if constexpr (EX) return fmaf(k2.hi, x, k2.lo * x);
   else return k2.hi * x;
 }
@@ -238,6 +251,26 @@ __device__ __forceinline__ double probe_round(double d, const StepParams& p) {
     return double(__half2float(__float2half_rn(float(d) * p.h_enc[I])) * p.h_dec[I]);
   return d;
 }
+
+// FP64 storage, float-float arithmetic: the double is split with integer
+// operations and the deviation from w_i taken in float-float; the store adds
+// w_i back and rounds to the nearest double (lbm_df.cuh).
+template <> struct Codec<P_FP64DF> {
+  using T = double;
+  using R = DF;
+  template <class L, int I>
+  __device__ __forceinline__ static R decode(T v, const StepParams&) {
+    constexpr DF w = DF(L::W(I));
+    return df_split(v) - w;
+  }
+  template <class L, int I>
+  __device__ __forceinline__ static T encode(R d, const StepParams&) {
+    constexpr DF w = DF(L::W(I));
+    return df_to_double(d + w);
+  }
+  __device__ __forceinline__ static T load(const T* ptr, const StepParams&) { return __ldg(ptr); }
+  __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
+};
 
 template <> struct Codec<P_FP32S> {
   using T = float;

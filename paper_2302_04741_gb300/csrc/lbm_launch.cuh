@@ -131,11 +131,13 @@ struct Ops {
   case PP * 4 + FF:                                                                      \
     e = cudaLaunchKernelEx(&cfg, k_step<L, PP, FF>, (const T<PP>*)fin, (T<PP>*)fout, p); \
     break;
-    // FO 3: force order 2 with the sigma-bar terms (plain kernel only)
+    // FO 3: force order 2 with the sigma-bar terms (plain kernel only);
+    // P 3: FP64 storage with float-float arithmetic
     switch (P * 4 + FO) {
       LBM_STEP_CASE(0, 0) LBM_STEP_CASE(0, 1) LBM_STEP_CASE(0, 2) LBM_STEP_CASE(0, 3)
       LBM_STEP_CASE(1, 0) LBM_STEP_CASE(1, 1) LBM_STEP_CASE(1, 2) LBM_STEP_CASE(1, 3)
       LBM_STEP_CASE(2, 0) LBM_STEP_CASE(2, 1) LBM_STEP_CASE(2, 2) LBM_STEP_CASE(2, 3)
+      LBM_STEP_CASE(3, 0) LBM_STEP_CASE(3, 1) LBM_STEP_CASE(3, 2) LBM_STEP_CASE(3, 3)
       default: return cudaErrorInvalidValue;
     }
 #undef LBM_STEP_CASE

@@ -1,0 +1,47 @@
+"""Runs a few plain steps of one configuration (for profilers: a fixed,
+small launch sequence of the step kernel).
+
+    python -m paper_2302_04741_gb300.run_steps --config rb2d --precision fp64 --steps 3
+"""
+import argparse
+
+from paper_2302_04741_gb300 import workloads as W
+
+PRECISIONS = {"fp64": W.FP64, "fp32": W.FP32_SHIFTED, "fp16": W.FP16_SCALED}
+
+
+def workload(config, precision, nx=None, ny=None, nz=None):
+    if config == "rb2d":
+        return W.rayleigh_benard(nx=nx or 1024, ny=ny or 512, precision=precision)
+    if config == "rb3d":
+        return W.rayleigh_benard(nx=nx or 512, ny=ny or 512, nz=nz or 256, lattice=W.D3Q39, tau=0.55,
+                                 g=-5e-6, T_bottom=1.02, T_top=0.98, seed=5, precision=precision)
+    raise ValueError(config)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="rb2d", choices=["rb2d", "rb3d"])
+    ap.add_argument("--precision", default="fp32", choices=sorted(PRECISIONS))
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--nx", type=int, default=None)
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=None)
+    ap.add_argument("--arith", type=int, default=None, help="lbm_options.fp64_arith (FP64 storage)")
+    args = ap.parse_args()
+    import torch
+    import paper_2302_04741_gb300 as lbm
+    from paper_2302_04741_gb300 import build
+    build.build()
+    w = workload(args.config, PRECISIONS[args.precision], args.nx, args.ny, args.nz)
+    kw = {} if args.arith is None else {"fp64_arith": args.arith}
+    sim = lbm.Sim(w, overlap_steps=0, **kw).init()
+    sim.step(args.steps)
+    torch.cuda.synchronize()
+    st = sim.conserved()
+    print("ok", args.config, args.precision, args.steps, "mass", st[1])
+    sim.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -67,6 +67,13 @@ def test_default_options_and_validation(libpath):
     o.include_sigma = 1
     with pytest.raises(lbm.LbmError):
         lbm.lbm_create(0, 8, 8, 1, 0.8, None, o)
+    # float-float step arithmetic: FP64 storage, plain kernel, no storage probe
+    for kw in (dict(precision=1, fp64_arith=1), dict(fp64_arith=2), dict(fp64_arith=1, storage_probe=1),
+               dict(fp64_arith=1, kernel=lbm.LBM_KERNEL_TMA)):
+        o = lbm.options(**kw)
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_create(0, 8, 8, 1, 0.8, None, o)
+        assert ei.value.status == lbm.LBM_EINVAL
     # the storage probe: FP64 storage, a float codec's format, the plain kernel
     for kw in (dict(precision=1, storage_probe=1), dict(storage_probe=3), dict(storage_probe=-1),
                dict(storage_probe=2, kernel=lbm.LBM_KERNEL_TMA)):

@@ -87,6 +87,19 @@ def test_fp64_step_parity(case):
     assert np.max(np.abs(fg - fo)) < 1e-14
 
 
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fp64_float_pair_step_parity(case):
+    """FP64 storage with the float-float step (lbm_options.fp64_arith): the
+    FP64 field tolerance against the oracle, and per population within
+    1e-12 of the oracle (the float-float arithmetic carries ~48 bits)."""
+    w = make_case(case, 0)
+    w["fp64_arith"] = lbm.LBM_ARITH_FLOAT_PAIR
+    sim, ref = run_both(w, 12)
+    check_fields(sim, ref, w, TOL[0])
+    perm = perm_to_oracle(w["lattice"])
+    assert np.max(np.abs(sim.populations() - ref.pulled()[perm])) < 1e-12
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("case", CASES[:1] + CASES[3:6] + CASES[6:7], ids=lambda c: str(c[0]) if isinstance(c, tuple) else str(c))
 def test_reduced_precision_parity(case, precision):
@@ -162,6 +175,24 @@ def test_sigma_bar_parity(case, precision):
         assert np.max(np.abs(plain.pulled()[perm] - fo)) > 1e-11
 
 
+@pytest.mark.parametrize("case", MU_CASES, ids=[c[0] for c in MU_CASES])
+def test_float_pair_sigma_and_constant_mu(case):
+    """The float-float step with the sigma-bar terms and with constant mu."""
+    for extra in (dict(mu=0.25, tau=5.0), dict(include_sigma=True)):
+        w = make_case(case, 0)
+        if extra.get("include_sigma"):
+            if case[4] != 2:
+                continue
+            D = W.dims(w["lattice"])
+            w["g"] = {"kind": W.G_UNIFORM, "g0": (4e-4, -3e-4, 2e-4)[:D] + (0.0,) * (3 - D)}
+        w.update(extra)
+        w["fp64_arith"] = lbm.LBM_ARITH_FLOAT_PAIR
+        sim, ref = run_both(w, 12)
+        check_fields(sim, ref, w, TOL[0])
+        fo = ref.pulled()[perm_to_oracle(w["lattice"])]
+        assert np.max(np.abs(sim.populations() - fo)) < 1e-12
+
+
 def test_sigma_bar_with_constant_mu():
     w = make_case(CASES[4], 0)
     w["g"] = {"kind": W.G_UNIFORM, "g0": (3e-4, -5e-4, 0.0)}
@@ -208,9 +239,12 @@ def test_init_roundtrip(lat, shape, bc, precision):
 
 
 @pytest.mark.parametrize("fo", [2, 1])
-def test_kolmogorov_64_fp64_2000_steps(fo):
-    """The 64x64 FP64 Kolmogorov configuration (third-moment term on/off), full run."""
+@pytest.mark.parametrize("arith", [0, 1])
+def test_kolmogorov_64_fp64_2000_steps(fo, arith):
+    """The 64x64 FP64 Kolmogorov configuration (third-moment term on/off), full
+    run, with IEEE double and with float-float step arithmetic."""
     w = W.kolmogorov(force_order=fo)
+    w["fp64_arith"] = arith
     sim, ref = run_both(w, 2000)
     err = check_fields(sim, ref, w, TOL[0])
     print("kolmogorov fo", fo, err)
