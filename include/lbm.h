@@ -244,6 +244,22 @@ int lbm_step(lbm_ctx *ctx, int n);
  * device buffer.  Synchronises the stream. */
 int lbm_moments(lbm_ctx *ctx, double *rho, double *u, double *T, double *q);
 
+/* lbm_moments without synchronising: the same fields (Sec. 2), enqueued on
+ * the context's stream and written when the stream reaches them.  Outputs
+ * must be device memory or page-locked host memory (LBM_EINVAL otherwise);
+ * the caller waits for the stream (or an event recorded after this call)
+ * before reading them.  Lets a caller overlap the readout with other work,
+ * e.g. the next steps of a batch this context has left. */
+int lbm_moments_async(lbm_ctx *ctx, double *rho, double *u, double *T, double *q);
+
+/* Changes the collision divisor tau (tau-hat of Eq. lbm, > 1/2) and the
+ * uniform body-force acceleration g (Eq. BGK; NULL = no force) of a context
+ * created with a uniform or no force, for the steps that follow.  The
+ * buffers stay: a caller that serves many simulations of one grid size can
+ * re-use a context (lbm_set_params, then lbm_init) without any device
+ * allocation.  LBM_EINVAL for tau <= 1/2 or a non-uniform force. */
+int lbm_set_params(lbm_ctx *ctx, double tau, const lbm_gfield *g);
+
 /* Global sums over the grid (deterministic for a fixed grid) of the
  * conserved moments of Eq. rut (discrete form Eq. rut1): mass = sum rho,
  * mom[D] = sum rho u, energy = sum rho (|u|^2 + D theta)/2, all physical

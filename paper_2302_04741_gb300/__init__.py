@@ -86,6 +86,8 @@ def lib():
         L.lbm_set_solid.argtypes = [_vp, ctypes.POINTER(ctypes.c_ubyte), _dp]
         L.lbm_moments.argtypes = [_vp, _vp, _vp, _vp, _vp]
         L.lbm_conserved.argtypes = [_vp, _dp, _dp, _dp]
+        L.lbm_moments_async.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.lbm_set_params.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(lbm_gfield)]
         for name in ("lbm_get_populations", "lbm_get_state", "lbm_set_state"):
             getattr(L, name).argtypes = [_vp, _vp]
         L.lbm_step_kernel.argtypes = [_vp]
@@ -212,6 +214,17 @@ def lbm_set_solid(ctx, solid, T_wall):
 
 def lbm_moments(ctx, rho=None, u=None, T=None, q=None):
     _check(lib().lbm_moments(ctx, _ptr(rho), _ptr(u), _ptr(T), _ptr(q)), ctx)
+
+
+def lbm_moments_async(ctx, rho=None, u=None, T=None, q=None):
+    """Enqueues the moments into device (or page-locked) float64 tensors."""
+    _check(lib().lbm_moments_async(ctx, _ptr(rho), _ptr(u), _ptr(T), _ptr(q)), ctx)
+
+
+def lbm_set_params(ctx, tau, g=None):
+    """New tau-hat and uniform force (workload-style dict or None) for a context."""
+    gf = make_gfield(g) if isinstance(g, dict) else g
+    _check(lib().lbm_set_params(ctx, float(tau), ctypes.byref(gf) if gf is not None else None), ctx)
 
 
 def lbm_conserved(ctx, D, raise_unstable=True):

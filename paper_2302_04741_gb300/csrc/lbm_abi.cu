@@ -886,6 +886,52 @@ int lbm_moments(lbm_ctx* c, double* rho, double* u, double* T, double* q) {
   return LBM_OK;
 }
 
+int lbm_moments_async(lbm_ctx* c, double* rho, double* u, double* T, double* q) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_moments_async before lbm_init");
+  double* outs[4] = {rho, u, T, q};
+  double* dst[4];
+  for (int k = 0; k < 4; ++k) {
+    dst[k] = outs[k] ? device_view(outs[k]) : nullptr;
+    if (outs[k] && !dst[k])
+      return fail(c, LBM_EINVAL, "lbm_moments_async needs device or page-locked outputs");
+  }
+  LBM_CUDA(c, cudaSetDevice(c->device));
+  if (c->slab) {  // through the buffer layout, then the slab's own layers
+    int rc = ensure_tmp(c);
+    if (rc) return rc;
+    const size_t N = (size_t)c->N;
+    double* t[4] = {c->tmp, c->tmp + N, c->tmp + (1 + c->D) * N, c->tmp + (2 + c->D) * N};
+    LBM_CUDA(c, c->ops->moments(c->opt.precision, c->f[c->cur], rho ? t[0] : nullptr, u ? t[1] : nullptr,
+                                T ? t[2] : nullptr, q ? t[3] : nullptr, c->fo, c->p, c->stream));
+    const int rows[4] = {1, c->D, 1, c->D};
+    for (int k = 0; k < 4; ++k)
+      if (outs[k]) LBM_CUDA(c, copy_rows(c, dst[k], t[k], rows[k], true));
+    return LBM_OK;
+  }
+  LBM_CUDA(c, c->ops->moments(c->opt.precision, c->f[c->cur], dst[0], dst[1], dst[2], dst[3], c->fo, c->p,
+                              c->stream));
+  return LBM_OK;
+}
+
+int lbm_set_params(lbm_ctx* c, double tau, const lbm_gfield* g) {
+  if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBM_EINVAL, "tau-hat must be > 1/2 (got %g)", tau);
+  if (c->p.gkind != lbm::G_UNIFORM)
+    return fail(c, LBM_EINVAL, "lbm_set_params serves contexts created with a uniform (or no) force");
+  if (g && g->kind != LBM_G_UNIFORM) return fail(c, LBM_EINVAL, "lbm_set_params takes a uniform force");
+  c->tau = tau;
+  c->p.omega = 1.0 / tau;
+  c->p.omega_f = (float)c->p.omega;
+  for (int a = 0; a < 3; ++a) {
+    c->p.g0[a] = (g && a < c->D) ? g->g0[a] : 0.0;
+    c->p.g0_f[a] = (float)c->p.g0[a];
+  }
+  drop_graphs(c);
+  lbm::batch_mark_dirty(c->batch);
+  return LBM_OK;
+}
+
 int lbm_conserved(lbm_ctx* c, double* mass, double* mom, double* energy) {
   if (!c) return fail(nullptr, LBM_EINVAL, "ctx is NULL");
   if (!c->initialised) return fail(c, LBM_ESTATE, "lbm_conserved before lbm_init");

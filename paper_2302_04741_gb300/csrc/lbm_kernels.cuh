@@ -607,11 +607,23 @@ __device__ __forceinline__ void ff_mac(FF& acc, float hi, float lo) {
   }
 }
 
+// Symmetric 3x3 (xx, yy, zz, xy, xz, yz) times a vector.
+template <class R>
+__device__ __forceinline__ void sym_mul(const R (&S)[6], const R (&v)[3], R (&o)[3]) {
+  o[0] = S[0] * v[0] + S[3] * v[1] + S[4] * v[2];
+  o[1] = S[3] * v[0] + S[1] * v[1] + S[5] * v[2];
+  o[2] = S[4] * v[0] + S[5] * v[1] + S[2] * v[2];
+}
+
+// The same raw moments as float-float values: each compensated pair s + c
+// renormalised (an exact two-sum, since c may exceed ulp(s) after a
+// cancellation).
 template <class L>
-__device__ __forceinline__ HeatMoments<L> heat_moments_ff(const float (&d)[L::Q]) {
+__device__ __forceinline__ void heat_moments_df(const float (&d)[L::Q], DF& m0, DF (&m1)[3], DF (&m2)[6],
+                                                DF (&m3)[3]) {
   constexpr int NP = (L::Q - 1) / 2;
-  FF m0, m1[3], m2[6], m3[3];
-  m0.s = d[0];
+  FF f0, f1[3], f2[6], f3[3];
+  f0.s = d[0];
   static_for<0, NP>([&](auto K) {
     constexpr int ip = 2 * K + 1, im = ip + 1;
     constexpr int ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
@@ -619,38 +631,109 @@ __device__ __forceinline__ HeatMoments<L> heat_moments_ff(const float (&d)[L::Q]
     float sh, sl, ah, al;
     two_sum(d[ip], d[im], sh, sl);
     two_sum(d[ip], -d[im], ah, al);
-    ff_mac<1>(m0, sh, sl);
-    ff_mac<ex>(m1[0], ah, al);
-    ff_mac<ey>(m1[1], ah, al);
-    ff_mac<ex * ex>(m2[0], sh, sl);
-    ff_mac<ey * ey>(m2[1], sh, sl);
-    ff_mac<ex * ey>(m2[3], sh, sl);
-    ff_mac<e2 * ex>(m3[0], ah, al);
-    ff_mac<e2 * ey>(m3[1], ah, al);
+    ff_mac<1>(f0, sh, sl);
+    ff_mac<ex>(f1[0], ah, al);
+    ff_mac<ey>(f1[1], ah, al);
+    ff_mac<ex * ex>(f2[0], sh, sl);
+    ff_mac<ey * ey>(f2[1], sh, sl);
+    ff_mac<ex * ey>(f2[3], sh, sl);
+    ff_mac<e2 * ex>(f3[0], ah, al);
+    ff_mac<e2 * ey>(f3[1], ah, al);
     if constexpr (L::D == 3) {
-      ff_mac<ez>(m1[2], ah, al);
-      ff_mac<ez * ez>(m2[2], sh, sl);
-      ff_mac<ex * ez>(m2[4], sh, sl);
-      ff_mac<ey * ez>(m2[5], sh, sl);
-      ff_mac<e2 * ez>(m3[2], ah, al);
+      ff_mac<ez>(f1[2], ah, al);
+      ff_mac<ez * ez>(f2[2], sh, sl);
+      ff_mac<ex * ez>(f2[4], sh, sl);
+      ff_mac<ey * ez>(f2[5], sh, sl);
+      ff_mac<e2 * ez>(f3[2], ah, al);
     }
   });
-  HeatMoments<L> h;
-  auto v = [](const FF& f) { return double(f.s) + double(f.c); };
-  h.m0 = v(m0);
+  auto v = [](const FF& f) {
+    DF r;
+    df_two_sum(f.s, f.c, r.hi, r.lo);
+    return r;
+  };
+  m0 = v(f0);
   for (int a = 0; a < 3; ++a) {
-    h.m1[a] = v(m1[a]);
-    h.m3[a] = v(m3[a]);
+    m1[a] = v(f1[a]);
+    m3[a] = v(f3[a]);
   }
-  for (int k = 0; k < 6; ++k) h.m2[k] = v(m2[k]);
-  return h;
+  for (int c = 0; c < 6; ++c) m2[c] = v(f2[c]);
 }
 
-// Symmetric 3x3 (xx, yy, zz, xy, xz, yz) times a vector.
-__device__ __forceinline__ void sym_mul(const double (&S)[6], const double (&v)[3], double (&o)[3]) {
-  o[0] = S[0] * v[0] + S[3] * v[1] + S[4] * v[2];
-  o[1] = S[3] * v[0] + S[1] * v[1] + S[5] * v[2];
-  o[2] = S[4] * v[0] + S[5] * v[1] + S[2] * v[2];
+__device__ __forceinline__ double out_double(double x) { return x; }
+__device__ __forceinline__ double out_double(DF x) { return df_to_double(x); }
+
+// rho, u, T and q of one site from the raw moments of its pulled deviations
+// (see the comment above HeatMoments), in the arithmetic type R: double for
+// FP64 storage, float-float (~48 bits, lbm_df.cuh) for the float codecs,
+// whose FP64 combination ran at the FP64 units' rate; each output is one
+// rounding to double.
+template <class L, class R>
+__device__ __forceinline__ void write_moments(R m0, const R (&m1)[3], const R (&m2)[6], const R (&m3)[3],
+                                              const R (&g)[3], int site, size_t N, int force_order,
+                                              const StepParams& p, double* __restrict__ rho,
+                                              double* __restrict__ u, double* __restrict__ T,
+                                              double* __restrict__ q) {
+  constexpr int D = L::D;
+  const R c = R(L::c), c2 = R(L::c2);
+  const R r = R(1) + m0, ir = R(1) / r;
+  R J[3], uu[3];
+  for (int a = 0; a < 3; ++a) {
+    J[a] = c * m1[a];  // sum f~ xi = rho u~
+    uu[a] = J[a] * ir + R(0.5) * g[a];
+  }
+  const R k2 = m2[0] + m2[1] + m2[2];
+  const R ut2 = (J[0] * J[0] + J[1] * J[1] + J[2] * J[2]) * ir * ir;
+  const R g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  const R Th = ((c2 * k2 - R(D) * m0) * ir - ut2) * R(1.0 / D) + g2 * R(0.25 / D);
+  if (rho) rho[site] = out_double(r);
+  if (T) T[site] = out_double(R(1) + Th);
+  if (u)
+    for (int a = 0; a < D; ++a) u[a * N + site] = out_double(uu[a]);
+  if (!q) return;
+  const R om = site_omega<R>(p, r, R(1) + Th);
+  const R u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+  const R ug = uu[0] * g[0] + uu[1] * g[1] + uu[2] * g[2];
+  const R uJ = uu[0] * J[0] + uu[1] * J[1] + uu[2] * J[2];
+  // sum f~ |c|^2 c with P = c^2 m2 (so sum f~ xi xi = delta + P)
+  R Pm[6], Pu[3];
+  for (int k = 0; k < 6; ++k) Pm[k] = c2 * m2[k];
+  sym_mul<R>(Pm, uu, Pu);
+  const R c3 = R(L::c * L::c2);
+  R C3[3];
+  for (int a = 0; a < 3; ++a)
+    C3[a] = c3 * m3[a] - R(D + 2) * uu[a] - uu[a] * (c2 * k2) - R(2) * Pu[a] + R(2) * uu[a] * uJ +
+            u2 * J[a] - u2 * uu[a] * r;
+  // sum F |c|^2 c
+  R FC3[3];
+  const R th = R(1) + Th;
+  if (force_order >= 2) {
+    for (int a = 0; a < 3; ++a) FC3[a] = R(D + 2) * r * th * g[a];
+    if (force_order == 3) {
+      // S = rho (u u + theta delta) - sigma-bar, sigma-bar = -(1 - om/2) S_st
+      R Sst[6], Sg[3];
+      const R iso = fma(r, Th, m0);
+      const R hr = R(0.5) * r;
+      auto conv = [&](int a, int b) { return hr * (uu[a] * (g[b] - uu[b]) + uu[b] * (g[a] - uu[a])); };
+      Sst[0] = Pm[0] - iso + conv(0, 0);
+      Sst[1] = Pm[1] - iso + conv(1, 1);
+      Sst[2] = D == 3 ? Pm[2] - iso + conv(2, 2) : R(0);
+      Sst[3] = Pm[3] + conv(0, 1);
+      Sst[4] = D == 3 ? Pm[4] + conv(0, 2) : R(0);
+      Sst[5] = D == 3 ? Pm[5] + conv(1, 2) : R(0);
+      sym_mul<R>(Sst, g, Sg);
+      const R kf = R(1) - R(0.5) * om;
+      for (int a = 0; a < 3; ++a) FC3[a] += R(2) * kf * Sg[a];
+    }
+  } else {
+    // S = rho delta; M2 = rho (g u + u g) at order 1, 0 at order 0
+    for (int a = 0; a < 3; ++a) {
+      FC3[a] = R(D + 2) * r * g[a] + R(2) * r * uu[a] * ug + r * u2 * g[a];
+      if (force_order == 1) FC3[a] -= R(2) * r * uu[a] * ug + R(2) * r * (g[a] * u2 + uu[a] * ug);
+    }
+  }
+  const R kq = R(0.5) * (R(1) - R(0.5) * om);
+  for (int a = 0; a < D; ++a) q[a * N + site] = out_double(kq * (C3[a] + R(0.5) * FC3[a]));
 }
 
 template <class L, int P>
@@ -674,80 +757,26 @@ __global__ void __launch_bounds__(128) k_moments(const typename Codec<P>::T* __r
     }
     return;
   }
-  HeatMoments<L> h;
   if (P != P_FP64 && !p.solid) {
-    // float storage: the deviations are exact floats; sum them without FP64
+    // float storage: the deviations are exact floats; compensated float-pair
+    // sums and a float-float combination, no FP64 arithmetic but the final
+    // rounding of each output
     float d[Q];
     pull<L, P, float>(fin, p, x, y, z, d);
-    h = heat_moments_ff<L>(d);
-  } else {
-    double d[Q];
-    if (p.solid) pull_solid<L, P, double>(fin, p, x, y, z, site, d);
-    else pull<L, P, double>(fin, p, x, y, z, d);
-    h = heat_moments<L>(d);
+    DF m0, m1[3], m2[6], m3[3];
+    heat_moments_df<L>(d, m0, m1, m2, m3);
+    DF g[3];
+    site_force_r<D, DF>(p, x, y, z, site, g);
+    write_moments<L, DF>(m0, m1, m2, m3, g, site, N, force_order, p, rho, u, T, q);
+    return;
   }
+  double d[Q];
+  if (p.solid) pull_solid<L, P, double>(fin, p, x, y, z, site, d);
+  else pull<L, P, double>(fin, p, x, y, z, d);
+  const HeatMoments<L> h = heat_moments<L>(d);
   double g[3];
   site_force<D>(p, x, y, z, site, g);
-  // mid-point state (R1), as in the step kernel
-  const double c = L::c, c2 = L::c2;
-  const double r = 1.0 + h.m0, ir = 1.0 / r;
-  double J[3], uu[3];
-  for (int a = 0; a < 3; ++a) {
-    J[a] = c * h.m1[a];  // sum f~ xi = rho u~
-    uu[a] = J[a] * ir + 0.5 * g[a];
-  }
-  const double k2 = h.m2[0] + h.m2[1] + h.m2[2];
-  const double ut2 = (J[0] * J[0] + J[1] * J[1] + J[2] * J[2]) * ir * ir;
-  const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-  const double Th = ((c2 * k2 - double(D) * h.m0) * ir - ut2) * (1.0 / D) + g2 * (0.25 / D);
-  if (rho) rho[site] = r;
-  if (T) T[site] = 1.0 + Th;
-  if (u)
-    for (int a = 0; a < D; ++a) u[a * N + site] = uu[a];
-  if (!q) return;
-  const double om = site_omega<double>(p, r, 1.0 + Th);
-  const double u2 = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
-  const double ug = uu[0] * g[0] + uu[1] * g[1] + uu[2] * g[2];
-  const double uJ = uu[0] * J[0] + uu[1] * J[1] + uu[2] * J[2];
-  // sum f~ |c|^2 c with P = c^2 m2 (so sum f~ xi xi = delta + P)
-  double Pm[6], Pu[3];
-  for (int k = 0; k < 6; ++k) Pm[k] = c2 * h.m2[k];
-  sym_mul(Pm, uu, Pu);
-  const double c3 = c * c2;
-  double C3[3];
-  for (int a = 0; a < 3; ++a)
-    C3[a] = c3 * h.m3[a] - double(D + 2) * uu[a] - uu[a] * (c2 * k2) - 2.0 * Pu[a] +
-            2.0 * uu[a] * uJ + u2 * J[a] - u2 * uu[a] * r;
-  // sum F |c|^2 c
-  double FC3[3];
-  const double th = 1.0 + Th;
-  if (force_order >= 2) {
-    for (int a = 0; a < 3; ++a) FC3[a] = double(D + 2) * r * th * g[a];
-    if (force_order == 3) {
-      // S = rho (u u + theta delta) - sigma-bar, sigma-bar = -(1 - om/2) S_st
-      double Sst[6], Sg[3];
-      const double iso = fma(r, Th, h.m0);
-      const double hr = 0.5 * r;
-      auto conv = [&](int a, int b) { return hr * (uu[a] * (g[b] - uu[b]) + uu[b] * (g[a] - uu[a])); };
-      Sst[0] = Pm[0] - iso + conv(0, 0);
-      Sst[1] = Pm[1] - iso + conv(1, 1);
-      Sst[2] = D == 3 ? Pm[2] - iso + conv(2, 2) : 0.0;
-      Sst[3] = Pm[3] + conv(0, 1);
-      Sst[4] = D == 3 ? Pm[4] + conv(0, 2) : 0.0;
-      Sst[5] = D == 3 ? Pm[5] + conv(1, 2) : 0.0;
-      sym_mul(Sst, g, Sg);
-      const double kf = 1.0 - 0.5 * om;
-      for (int a = 0; a < 3; ++a) FC3[a] += 2.0 * kf * Sg[a];
-    }
-  } else {
-    // S = rho delta; M2 = rho (g u + u g) at order 1, 0 at order 0
-    for (int a = 0; a < 3; ++a) {
-      FC3[a] = double(D + 2) * r * g[a] + 2.0 * r * uu[a] * ug + r * u2 * g[a];
-      if (force_order == 1) FC3[a] -= 2.0 * r * uu[a] * ug + 2.0 * r * (g[a] * u2 + uu[a] * ug);
-    }
-  }
-  const double kq = 0.5 * (1.0 - 0.5 * om);
-  for (int a = 0; a < D; ++a) q[a * N + site] = kq * (C3[a] + 0.5 * FC3[a]);
+  write_moments<L, double>(h.m0, h.m1, h.m2, h.m3, g, site, N, force_order, p, rho, u, T, q);
 }
 
 // ------------------------------------------------------ conservation sums

@@ -540,8 +540,12 @@ def test_wave_kernel_rejections():
 @pytest.mark.parametrize("lat,shape,fo", [(0, (96, 24, 1), 2), (0, (80, 20, 1), 1), (1, (24, 20, 16), 2)])
 def test_float_storage_moments_match_fp64_sums(lat, shape, fo):
     """For float storage the diagnostic sums the deviations as compensated
-    float pairs; an all-fluid solid mask sends the same state through the FP64
-    summation instead.  Both give the same moments to ~1e-14."""
+    float pairs and combines them in float-float arithmetic (~48 bits); an
+    all-fluid solid mask sends the same state through the FP64 summation and
+    combination instead.  rho, u and T agree to 1e-13 relative; q, the small
+    remainder of a cancelling combination, agrees to 2^-40 of the size of
+    its terms, sum_i |f~_i - w_i| |xi_i - u|^3 (both far below the 6e-8 of the
+    float storage itself)."""
     w = workload(lat, shape, seed=17, precision=1, force_order=fo)
     a = lbm.Sim(w).init()
     b = lbm.Sim(w)
@@ -552,9 +556,14 @@ def test_float_storage_moments_match_fp64_sums(lat, shape, fo):
     np.testing.assert_array_equal(a.populations(), b.populations())
     ma, mb = a.moments(), b.moments()
     for name, x, y in zip(("rho", "u", "T"), ma, mb):
-        np.testing.assert_allclose(x, y, rtol=1e-14, atol=1e-16, err_msg=name)
-    dq = np.max(np.abs(ma[3] - mb[3]))
-    assert dq < 1e-14 * max(np.max(np.abs(mb[3])), 1e-3), dq
+        np.testing.assert_allclose(x, y, rtol=1e-13, atol=1e-16, err_msg=name)
+    f = b.populations()
+    D = a.D
+    xi = a.c * a.e[:, :D].astype(float)
+    cc = xi[:, :, None] - mb[1][None, :, :]
+    scale = (np.abs(f - a.wts[:, None]) * np.sqrt((cc * cc).sum(axis=1)) ** 3).sum(axis=0)
+    dq = np.abs(ma[3] - mb[3]).max(axis=0)
+    assert np.all(dq <= 2.0 ** -40 * scale), float(np.max(dq / scale))
 
 
 def _create(lat=0, nx=32, ny=16, nz=1, tau=0.8, **opt):

@@ -1,11 +1,14 @@
-"""Host logic of the continuous-batching server, with the device calls faked.
+"""Host logic of the continuous-batching server, with the device faked.
 
-The scheduler decides admission (arrival, free slot, free HBM), the number
-of steps per tick (never past the nearest completion) and retirement; none
-of that needs a GPU, so the library entry points it calls are replaced by a
-fake batch that only counts steps, and time is a fake clock that advances
-with the work.
+The scheduler decides admission (arrival, free slot, free HBM or an idle
+pooled context), the number of steps per tick (never past the nearest
+completion), the readout of completed requests and the re-use of their
+contexts; none of that needs a GPU, so the server's device-facing steps are
+replaced by a fake device that counts steps, keeps batch membership and free
+memory, and advances a fake clock with the work.
 """
+import collections
+
 import numpy as np
 import pytest
 
@@ -14,92 +17,92 @@ from paper_2302_04741_gb300 import serving, workloads as W
 
 
 class FakeSim:
-    live = []
-
-    def __init__(self, w, stream=None):
+    def __init__(self, w):
         self.w = w
         self.ctx = self
         self.steps = 0
-        self.closed = False
-        FakeSim.live.append(self)
-
-    def init(self):
-        return self
-
-    def moments(self):
-        n = int(np.prod(self.w["shape"]))
-        return np.ones(n), np.zeros((3, n)), np.ones(n), np.zeros((3, n))
-
-    def close(self):
-        self.closed = True
+        self.users = []
 
 
-class FakeDevice:
-    """Batch membership, step counts, a clock advanced by the work and the
-    free memory the admission check reads."""
+class FakeEvent:
+    def __init__(self, t):
+        self.t = t
 
-    def __init__(self, free_bytes, seconds_per_update=1e-10):
-        self.members = []
-        self.launches = []
-        self.t = 0.0
+
+class FakeServer(serving.Server):
+    """The real scheduler (run) over a fake device."""
+
+    def __init__(self, free_bytes, max_slots, tick_steps, reserve=0, seconds_per_update=1e-10):
+        self.precision, self.force_order, self.lattice = W.FP32_SHIFTED, 2, W.D3Q39
+        self.max_slots, self.hbm_reserve, self.tick_steps = max_slots, reserve, tick_steps
+        self.collect = ("rho", "u", "T", "q")
         self.free = free_bytes
         self.spu = seconds_per_update
+        self.t = 0.0
+        self.members = []
+        self.launches = []
+        self._setup()
 
     def clock(self):
         return self.t
 
-    def batch_add(self, b, ctx):
-        assert ctx not in self.members
-        self.members.append(ctx)
-        self.free -= serving.request_bytes(ctx.w, W.FP32_SHIFTED)
+    def _fits(self, req):
+        if self.pool[tuple(req.workload["shape"])]:
+            return True
+        return self.free - serving.request_bytes(req.workload, self.precision) >= self.hbm_reserve
 
-    def batch_remove(self, b, ctx):
-        self.members.remove(ctx)
-        self.free += serving.request_bytes(ctx.w, W.FP32_SHIFTED)
+    def _context(self, req):
+        idle = self.pool[tuple(req.workload["shape"])]
+        if idle:
+            sim = idle.pop()
+        else:
+            sim = FakeSim(req.workload)
+            self.contexts.append(sim)
+            self.free -= serving.request_bytes(req.workload, self.precision)
+        sim.steps = 0  # lbm_init resets the step count
+        sim.users.append(req.id)
+        return sim
 
-    def batch_step(self, b, n):
+    def _start(self, req):
+        assert req.sim not in self.members
+        self.members.append(req.sim)
+
+    def _tick(self, n, lups):
         assert self.members, "a tick with no resident grid"
         self.launches.append((n, len(self.members)))
         for m in self.members:
             m.steps += n
         self.t += n * sum(int(np.prod(m.w["shape"])) for m in self.members) * self.spu
+        self.ticks.append((n, lups, self.t, None))
+        return FakeEvent(self.t)
 
+    def _readout(self, req):
+        self.members.remove(req.sim)
+        self.pool[tuple(req.workload["shape"])].append(req.sim)
+        return serving.Readout(req, None, FakeEvent(self.t))
 
-class FakeTorchCuda:
-    def __init__(self, dev):
-        self.dev = dev
+    def _ready(self, rd):
+        return True
 
-    def mem_get_info(self):
-        return self.dev.free, 1 << 40
-
-
-class FakeTorch:
-    def __init__(self, dev):
-        self.cuda = FakeTorchCuda(dev)
-
-
-class FakeStream:
-    cuda_stream = 0
-
-    def synchronize(self):
+    def _wait(self, event):
         pass
 
+    def _collect(self, rd):
+        n = rd.req.sites
+        return {"rho": np.ones(n), "u": np.zeros((3, n)), "T": np.ones(n), "q": np.zeros((3, n)),
+                "steps": rd.req.sim.steps}
 
-def make_server(monkeypatch, dev, max_slots, tick_steps, reserve=0):
-    monkeypatch.setattr(lbm, "Sim", FakeSim)
-    monkeypatch.setattr(lbm, "lbm_batch_add", dev.batch_add)
-    monkeypatch.setattr(lbm, "lbm_batch_remove", dev.batch_remove)
-    monkeypatch.setattr(lbm, "lbm_batch_step", dev.batch_step)
+    def _busy_seconds(self):
+        return self.t
+
+
+@pytest.fixture(autouse=True)
+def fake_step_count(monkeypatch):
     monkeypatch.setattr(lbm, "lbm_step_count", lambda ctx: ctx.steps)
-    monkeypatch.setattr(serving.time, "sleep", lambda s: setattr(dev, "t", dev.t + s))
-    s = serving.Server.__new__(serving.Server)
-    s.torch = FakeTorch(dev)
-    s.lattice, s.precision, s.force_order = W.D3Q39, W.FP32_SHIFTED, 2
-    s.max_slots, s.hbm_reserve, s.tick_steps = max_slots, reserve, tick_steps
-    s.graph_steps, s.collect = 10, ("rho", "u", "T", "q")
-    s.stream, s.batch = FakeStream(), None
-    s.resident, s.ticks, s.max_resident = [], [], 0
-    return s
+
+
+def fake_sleep(srv, monkeypatch):
+    monkeypatch.setattr(serving.time, "sleep", lambda s: setattr(srv, "t", srv.t + s))
 
 
 def trace(n, seed=4, rate=50.0, sides=(32, 48)):
@@ -108,49 +111,61 @@ def trace(n, seed=4, rate=50.0, sides=(32, 48)):
 
 @pytest.mark.parametrize("max_slots,tick", [(1, 100), (4, 64), (64, 1000)])
 def test_every_request_finishes_with_its_exact_step_count(monkeypatch, max_slots, tick):
-    FakeSim.live = []
-    dev = FakeDevice(free_bytes=1 << 40)
-    srv = make_server(monkeypatch, dev, max_slots, tick)
+    srv = FakeServer(1 << 40, max_slots, tick)
+    fake_sleep(srv, monkeypatch)
     reqs = serving.requests_from_trace(trace(30))
-    stats = srv.run(reqs, clock=dev.clock)
+    stats = srv.run(reqs, clock=srv.clock)
     assert stats["requests"] == 30
     for r in reqs:
         assert r.sim is None and r.done is not None and r.done >= r.arrival
         assert r.admitted >= r.arrival
-        assert set(r.result) == {"rho", "u", "T", "q"}
-    # no overshoot: every grid stopped exactly at its step count
-    done_steps = sorted(s.steps for s in FakeSim.live)
-    assert done_steps == sorted(r.steps for r in reqs)
-    assert all(s.closed for s in FakeSim.live)
+        assert {"rho", "u", "T", "q"} <= set(r.result)
+        # no overshoot: the grid stopped exactly at its step count
+        assert r.result["steps"] == r.steps
     # ticks never exceed the limit, and the resident count never the slots
-    assert all(1 <= n <= tick for n, _ in dev.launches)
-    assert all(k <= max_slots for _, k in dev.launches)
+    assert all(1 <= n <= tick for n, _ in srv.launches)
+    assert all(k <= max_slots for _, k in srv.launches)
     assert stats["max_resident"] <= max_slots
     assert stats["lattice_updates"] == sum(r.sites * r.steps for r in reqs)
-    assert not dev.members
+    assert not srv.members
+
+
+def test_contexts_are_pooled_per_grid_size(monkeypatch):
+    """Finished requests hand their context to the next request of the same
+    size: no more contexts exist than requests of a size ever resident at
+    once, and every context served requests of one size only."""
+    srv = FakeServer(1 << 40, 4, 64)
+    fake_sleep(srv, monkeypatch)
+    reqs = serving.requests_from_trace(trace(40, rate=500.0))
+    srv.run(reqs, clock=srv.clock)
+    by_size = collections.Counter(tuple(r.workload["shape"]) for r in reqs)
+    assert len(srv.contexts) <= sum(min(4, k) for k in by_size.values())
+    assert len(srv.contexts) < len(reqs)
+    for sim in srv.contexts:
+        sizes = {tuple(next(r for r in reqs if r.id == u).workload["shape"]) for u in sim.users}
+        assert len(sizes) == 1
 
 
 def test_admission_waits_for_device_memory(monkeypatch):
-    """With room for one request at a time (all of one size) the server never
+    """With room for one context (all requests of one size) the server never
     holds two, and requests are admitted in arrival order."""
-    FakeSim.live = []
     reqs = serving.requests_from_trace(trace(8, rate=1000.0, sides=(48,)))
     one = max(serving.request_bytes(r.workload, W.FP32_SHIFTED) for r in reqs)
-    dev = FakeDevice(free_bytes=one + one // 2)
-    srv = make_server(monkeypatch, dev, max_slots=64, tick_steps=100)
-    stats = srv.run(reqs, clock=dev.clock)
+    srv = FakeServer(one + one // 2, 64, 100)
+    fake_sleep(srv, monkeypatch)
+    stats = srv.run(reqs, clock=srv.clock)
     assert stats["requests"] == 8
     assert stats["max_resident"] == 1
+    assert len(srv.contexts) == 1
     order = sorted(reqs, key=lambda r: r.admitted)
     assert [r.id for r in order] == [r.id for r in sorted(reqs, key=lambda r: r.arrival)]
 
 
 def test_no_request_is_admitted_before_it_arrives(monkeypatch):
-    FakeSim.live = []
-    dev = FakeDevice(free_bytes=1 << 40, seconds_per_update=1e-12)
-    srv = make_server(monkeypatch, dev, max_slots=8, tick_steps=50)
+    srv = FakeServer(1 << 40, 8, 50, seconds_per_update=1e-12)
+    fake_sleep(srv, monkeypatch)
     reqs = serving.requests_from_trace(trace(12, rate=5.0))
-    srv.run(reqs, clock=dev.clock)
+    srv.run(reqs, clock=srv.clock)
     assert all(r.admitted >= r.arrival for r in reqs)
     # idle gaps were slept through, not spun with empty launches
-    assert all(k >= 1 for _, k in dev.launches)
+    assert all(k >= 1 for _, k in srv.launches)
