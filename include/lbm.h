@@ -346,12 +346,26 @@ int lbm_batch_get_config(const lbm_batch *b, int *block_x, int *sites_per_thread
 /* Advances every member by n steps (asynchronous on the batch's stream). */
 int lbm_batch_step(lbm_batch *b, int n);
 
+/* Halo staging (FP32-shifted batches, sites_per_thread 1): staged = 1 steps
+ * the batch with a kernel that, while it collides one tile of sites, copies
+ * the populations its threads pull for their next tile into shared memory
+ * with cp.async (two stages of Q x block_x floats; warps whose pulls wrap
+ * around x or reach a wall load directly).  The results are bit-identical
+ * to the plain batch kernel.  Returns LBM_EINVAL for FP16-scaled storage or
+ * sites_per_thread 2 (and lbm_batch_set_config rejects sites_per_thread 2
+ * while staging is on).  Default 0. */
+int lbm_batch_set_staging(lbm_batch *b, int staged);
+int lbm_batch_get_staging(const lbm_batch *b, int *staged);
+
 /* Autotuner: times trial_steps (even) batch steps for each block width in
- * {64, 128, 256} and 1 or 2 sites per thread, keeps the fastest, and caches
- * the choice per (lattice, precision, force order, member grid shapes) for
- * the process.  The trials are real steps: every member advances by
- * 6 * (trial_steps + 2) steps when the timing runs (0 on a cache hit).  The
- * chosen block width and sites per thread are returned (may be NULL). */
+ * {64, 128, 256} with 1 or 2 sites per thread and, for FP32-shifted storage,
+ * with halo staging (one site per thread), keeps the fastest, and caches the
+ * choice per (lattice, precision, force order, member grid shapes) for the
+ * process.  The trials are real steps: every member advances by
+ * 9 * (trial_steps + 2) steps (FP32-shifted) or 6 * (trial_steps + 2) steps
+ * (FP16-scaled) when the timing runs (0 on a cache hit).  The chosen block
+ * width and sites per thread are returned (may be NULL); the staging choice
+ * is read with lbm_batch_get_staging.  graph_steps is kept. */
 int lbm_batch_tune(lbm_batch *b, int trial_steps, int *block_x, int *sites_per_thread);
 
 const char *lbm_batch_last_error(const lbm_batch *b);

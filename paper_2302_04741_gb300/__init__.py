@@ -112,6 +112,8 @@ def lib():
         L.lbm_batch_get_config.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                            ctypes.POINTER(ctypes.c_int)]
         L.lbm_batch_step.argtypes = [_vp, ctypes.c_int]
+        L.lbm_batch_set_staging.argtypes = [_vp, ctypes.c_int]
+        L.lbm_batch_get_staging.argtypes = [_vp, ctypes.POINTER(ctypes.c_int)]
         L.lbm_batch_tune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int)]
         L.lbm_batch_last_error.argtypes = [_vp]
@@ -366,6 +368,16 @@ def lbm_batch_get_config(b):
     bx, spt, gs = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _bcheck(lib().lbm_batch_get_config(b, ctypes.byref(bx), ctypes.byref(spt), ctypes.byref(gs)), b)
     return bx.value, spt.value, gs.value
+
+
+def lbm_batch_set_staging(b, staged):
+    _bcheck(lib().lbm_batch_set_staging(b, int(staged)), b)
+
+
+def lbm_batch_get_staging(b):
+    v = ctypes.c_int()
+    _bcheck(lib().lbm_batch_get_staging(b, ctypes.byref(v)), b)
+    return v.value
 
 
 def lbm_batch_step(b, n):

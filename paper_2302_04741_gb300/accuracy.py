@@ -43,11 +43,14 @@ def rel_errors(a, b):
 
 
 def codec_accuracy(w, precision, checkpoints, stream=None, graph_steps=10, butterfly=1e-15,
-                   runs=("codec", "butterfly", "floor")):
+                   runs=("codec", "butterfly", "floor"), ref_arith=0):
     """Errors against FP64 of the runs named in ``runs`` at each step count of
     ``checkpoints`` (increasing).  ``w`` is a workload dict (its precision
-    field is ignored).  Returns {steps: {run: {rho, u, T, q}}} plus
-    "seconds"."""
+    field is ignored).  ref_arith: lbm_options.fp64_arith of the FP64
+    reference and butterfly runs (the float-float step agrees with IEEE
+    double to ~1e-12 and runs about twice as fast on GB300); the floor run
+    uses IEEE double (the storage probe).  Returns {steps: {run: {rho, u, T,
+    q}}} plus "seconds"."""
     import paper_2302_04741_gb300 as lbm
     from paper_2302_04741_gb300 import workloads as W
 
@@ -55,11 +58,12 @@ def codec_accuracy(w, precision, checkpoints, stream=None, graph_steps=10, butte
     t0 = time.time()
     try:
         mk = lambda ww, **kw: lbm.Sim(ww, stream=stream, graph_steps=graph_steps, **kw).init()
-        sims["fp64"] = mk(dict(w, precision=W.FP64))
+        sims["fp64"] = mk(dict(w, precision=W.FP64, fp64_arith=ref_arith))
         if "codec" in runs:
             sims["codec"] = mk(dict(w, precision=precision))
         if "butterfly" in runs:
-            sims["butterfly"] = mk(dict(w, precision=W.FP64, T=np.asarray(w["T"]) * (1.0 + butterfly)))
+            sims["butterfly"] = mk(dict(w, precision=W.FP64, fp64_arith=ref_arith,
+                                        T=np.asarray(w["T"]) * (1.0 + butterfly)))
         if "floor" in runs:
             sims["floor"] = mk(dict(w, precision=W.FP64), storage_probe=precision)
         out = {}
@@ -99,6 +103,7 @@ def main():
     ap.add_argument("--steps", type=int, required=True)
     ap.add_argument("--checkpoints", type=int, nargs="*", default=None)
     ap.add_argument("--runs", default="codec,butterfly,floor")
+    ap.add_argument("--ref-arith", type=int, default=0, help="fp64_arith of the FP64 reference")
     ap.add_argument("--out", default=None, help="write the result as JSON here")
     args = ap.parse_args()
     import torch
@@ -107,8 +112,9 @@ def main():
     w, prec = workload(args.config)
     cps = sorted(set((args.checkpoints or []) + [args.steps]))
     s = torch.cuda.Stream()
-    res = codec_accuracy(w, prec, cps, stream=s.cuda_stream, runs=tuple(args.runs.split(",")))
-    res = {"config": args.config, "precision": prec, "steps": args.steps,
+    res = codec_accuracy(w, prec, cps, stream=s.cuda_stream, runs=tuple(args.runs.split(",")),
+                         ref_arith=args.ref_arith)
+    res = {"config": args.config, "precision": prec, "steps": args.steps, "ref_arith": args.ref_arith,
            **{str(k): v for k, v in res.items()}}
     text = json.dumps(res, indent=1)
     print(text)

@@ -30,6 +30,7 @@ struct lbm_batch {
   cudaEvent_t staged = nullptr;  // last upload from the staging buffers
   bool dirty = true;
   int bx = 128, spt = 1, ctas = 0;
+  int stage = 0;  // 1: halo-staged kernel (FP32-shifted, one site per thread)
   int graph_steps = 0;
   cudaGraphExec_t graph = nullptr;
   std::string err;
@@ -73,7 +74,8 @@ void drop_graph(lbm_batch* b) {
 #endif
 int set_ctas(lbm_batch* b) {
   int bps = 0;
-  BCUDA(b, b->ops->batch_occupancy(b->precision, b->force_order, b->spt, b->bx, &bps));
+  if (b->stage) BCUDA(b, b->ops->batch_staged_occupancy(b->force_order, b->bx, &bps));
+  else BCUDA(b, b->ops->batch_occupancy(b->precision, b->force_order, b->spt, b->bx, &bps));
   if (bps < 1) return bfail(b, LBM_EINVAL, "batch kernel does not fit with block %d", b->bx);
   b->ctas = bps * b->nsm * LBM_BATCH_WAVES;
   return LBM_OK;
@@ -116,6 +118,11 @@ int upload(lbm_batch* b) {
 }
 
 int launch(lbm_batch* b, int k) {
+  if (b->stage) {
+    BCUDA(b, b->ops->batch_step_staged(b->force_order, b->d_grids, b->d_prefix, b->d_header, k, b->ctas,
+                                       b->bx, b->stream));
+    return LBM_OK;
+  }
   BCUDA(b, b->ops->batch_step(b->precision, b->force_order, b->spt, b->d_grids, b->d_prefix,
                               b->d_header, k, b->ctas, b->bx, b->stream));
   return LBM_OK;
@@ -138,9 +145,13 @@ int build_graph(lbm_batch* b) {
   return LBM_OK;
 }
 
-// Autotuner cache: (lattice, precision, order, grid shapes) -> (block, sites per thread).
+// Autotuner cache: (lattice, precision, order, grid shapes) -> (block, sites
+// per thread, staging).
+struct TuneChoice {
+  int bx, spt, stage;
+};
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+std::map<std::string, TuneChoice> g_tune_cache;
 
 std::string tune_key(const lbm_batch* b) {
   std::vector<std::string> shapes;
@@ -244,6 +255,8 @@ int lbm_batch_set_config(lbm_batch* b, int block_x, int sites_per_thread, int gr
     return bfail(b, LBM_EINVAL, "block_x must be a multiple of 32 in [32, 256]");
   if (sites_per_thread != 1 && sites_per_thread != 2)
     return bfail(b, LBM_EINVAL, "sites_per_thread must be 1 or 2");
+  if (b->stage && sites_per_thread != 1)
+    return bfail(b, LBM_EINVAL, "the halo-staged kernel steps one site per thread");
   if (graph_steps < 0 || graph_steps % 2) return bfail(b, LBM_EINVAL, "graph_steps must be even and >= 0");
   const bool changed = block_x != b->bx || sites_per_thread != b->spt || graph_steps != b->graph_steps;
   b->bx = block_x;
@@ -262,6 +275,27 @@ int lbm_batch_get_config(const lbm_batch* b, int* block_x, int* sites_per_thread
   if (block_x) *block_x = b->bx;
   if (sites_per_thread) *sites_per_thread = b->spt;
   if (graph_steps) *graph_steps = b->graph_steps;
+  return LBM_OK;
+}
+
+int lbm_batch_set_staging(lbm_batch* b, int staged) {
+  if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+  if (staged != 0 && staged != 1) return bfail(b, LBM_EINVAL, "staged must be 0 or 1");
+  if (staged && b->precision != LBM_FP32_SHIFTED)
+    return bfail(b, LBM_EINVAL, "halo staging serves FP32-shifted storage (4-byte populations)");
+  if (staged && b->spt != 1) return bfail(b, LBM_EINVAL, "halo staging needs sites_per_thread 1");
+  if (staged == b->stage) return LBM_OK;
+  const int old = b->stage;
+  b->stage = staged;
+  drop_graph(b);
+  const int rc = set_ctas(b);
+  if (rc) b->stage = old;
+  return rc;
+}
+
+int lbm_batch_get_staging(const lbm_batch* b, int* staged) {
+  if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+  if (staged) *staged = b->stage;
   return LBM_OK;
 }
 
@@ -300,53 +334,57 @@ int lbm_batch_tune(lbm_batch* b, int trial_steps, int* block_x, int* sites_per_t
   if (trial_steps < 2 || trial_steps % 2) return bfail(b, LBM_EINVAL, "trial_steps must be even and >= 2");
   if (b->members.empty()) return bfail(b, LBM_ESTATE, "batch is empty");
   const std::string key = tune_key(b);
-  int best_bx = 0, best_spt = 0;
+  TuneChoice best_c{0, 0, 0};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end()) {
-      best_bx = it->second.first;
-      best_spt = it->second.second;
-    }
+    if (it != g_tune_cache.end()) best_c = it->second;
   }
-  if (!best_bx) {
+  const int G = b->graph_steps;
+  if (!best_c.bx) {
+    // candidates: block 64 / 128 / 256 x one or two sites per thread, plus
+    // the halo-staged kernel (one site per thread) for FP32-shifted storage
+    std::vector<TuneChoice> cands;
+    for (int bx : {64, 128, 256}) {
+      for (int spt : {1, 2}) cands.push_back({bx, spt, 0});
+      if (b->precision == LBM_FP32_SHIFTED) cands.push_back({bx, 1, 1});
+    }
     cudaEvent_t e0, e1;
     BCUDA(b, cudaEventCreate(&e0));
     BCUDA(b, cudaEventCreate(&e1));
     float best = 1e30f;
-    const int G = b->graph_steps;
-    for (int bx : {64, 128, 256}) {
-      for (int spt : {1, 2}) {
-        int rc = lbm_batch_set_config(b, bx, spt, 0);
-        if (!rc) rc = lbm_batch_step(b, 2);  // warm-up
-        if (!rc) rc = cudaEventRecord(e0, b->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
-        if (!rc) rc = lbm_batch_step(b, trial_steps);
-        if (!rc) rc = cudaEventRecord(e1, b->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
-        if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? LBM_OK : LBM_ECUDA;
-        float ms = 0.f;
-        if (!rc) rc = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? LBM_OK : LBM_ECUDA;
-        if (rc) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return rc == LBM_ECUDA ? bfail(b, rc, "tuning trial failed") : rc;
-        }
-        if (ms < best) {
-          best = ms;
-          best_bx = bx;
-          best_spt = spt;
-        }
+    for (const TuneChoice& c : cands) {
+      int rc = lbm_batch_set_staging(b, 0);
+      if (!rc) rc = lbm_batch_set_config(b, c.bx, c.spt, 0);
+      if (!rc) rc = lbm_batch_set_staging(b, c.stage);
+      if (!rc) rc = lbm_batch_step(b, 2);  // warm-up
+      if (!rc) rc = cudaEventRecord(e0, b->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+      if (!rc) rc = lbm_batch_step(b, trial_steps);
+      if (!rc) rc = cudaEventRecord(e1, b->stream) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+      if (!rc) rc = cudaEventSynchronize(e1) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+      float ms = 0.f;
+      if (!rc) rc = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess ? LBM_OK : LBM_ECUDA;
+      if (rc) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc == LBM_ECUDA ? bfail(b, rc, "tuning trial failed") : rc;
+      }
+      if (ms < best) {
+        best = ms;
+        best_c = c;
       }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune_cache[key] = {best_bx, best_spt};
-    b->graph_steps = G;
+    g_tune_cache[key] = best_c;
   }
-  int rc = lbm_batch_set_config(b, best_bx, best_spt, b->graph_steps);
+  int rc = lbm_batch_set_staging(b, 0);
+  if (!rc) rc = lbm_batch_set_config(b, best_c.bx, best_c.spt, G);
+  if (!rc) rc = lbm_batch_set_staging(b, best_c.stage);
   if (rc) return rc;
-  if (block_x) *block_x = best_bx;
-  if (sites_per_thread) *sites_per_thread = best_spt;
+  if (block_x) *block_x = best_c.bx;
+  if (sites_per_thread) *sites_per_thread = best_c.spt;
   return LBM_OK;
 }
 

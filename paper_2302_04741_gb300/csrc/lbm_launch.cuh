@@ -42,6 +42,10 @@ struct LatticeOps {
   cudaError_t (*batch_occupancy)(int P, int FO, int spt, int bx, int* blocks_per_sm);
   cudaError_t (*batch_step)(int P, int FO, int spt, const BatchGrid* grids, const int* prefix,
                             const int* header, int k, int grid, int bx, cudaStream_t s);
+  // halo-staged batch step (FP32-shifted storage, one site per thread)
+  cudaError_t (*batch_staged_occupancy)(int FO, int bx, int* blocks_per_sm);
+  cudaError_t (*batch_step_staged)(int FO, const BatchGrid* grids, const int* prefix, const int* header,
+                                   int k, int grid, int bx, cudaStream_t s);
   // several steps in one persistent launch (FP32-shifted and FP16-scaled
   // storage; force orders 0..2); sync: 1 + n_lines zeroed words
   cudaError_t (*wave_occupancy)(int P, int FO, int* blocks_per_sm);
@@ -281,6 +285,34 @@ struct Ops {
     return cudaErrorInvalidValue;
   }
 
+  // same shared-memory stages as the prefetching step: [2][Q][bx] floats
+  static cudaError_t batch_staged_occupancy(int FO, int bx, int* bps) {
+    const int smem = (int)async_smem(bx);
+    cudaError_t e = cudaSuccess;
+#define LBM_SBOCC(FF)                                                                            \
+  if (FO == FF) {                                                                                \
+    e = cudaFuncSetAttribute(k_step_batch_staged<L, P_FP32S, FF>,                                \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);                 \
+    if (e == cudaSuccess)                                                                        \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_step_batch_staged<L, P_FP32S, FF>, \
+                                                        bx, smem);                               \
+    return e;                                                                                    \
+  }
+    LBM_SBOCC(0) LBM_SBOCC(1) LBM_SBOCC(2)
+#undef LBM_SBOCC
+    return cudaErrorInvalidValue;
+  }
+
+  static cudaError_t batch_step_staged(int FO, const BatchGrid* grids, const int* prefix, const int* header,
+                                       int k, int grid, int bx, cudaStream_t s) {
+    const size_t smem = async_smem(bx);
+    if (FO == 0) k_step_batch_staged<L, P_FP32S, 0><<<grid, bx, smem, s>>>(grids, prefix, header, k);
+    else if (FO == 1) k_step_batch_staged<L, P_FP32S, 1><<<grid, bx, smem, s>>>(grids, prefix, header, k);
+    else if (FO == 2) k_step_batch_staged<L, P_FP32S, 2><<<grid, bx, smem, s>>>(grids, prefix, header, k);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
+
   static cudaError_t wave_occupancy(int P, int FO, int* bps) {
 #define LBM_WOCC(PP, FF)                                                                         \
   if (P == PP && FO == FF)                                                                       \
@@ -333,7 +365,8 @@ struct Ops {
   static LatticeOps table() {
     return LatticeOps{L::Q, L::D, &step, &init, &moments, &conserved, &conserved_final, &pulled, &state,
                       &tma_smem, &tma_prepare, &step_tma, &async_occupancy, &step_async,
-                      &batch_occupancy, &batch_step, &wave_occupancy, &step_wave};
+                      &batch_occupancy, &batch_step, &batch_staged_occupancy, &batch_step_staged,
+                      &wave_occupancy, &step_wave};
   }
 };
 

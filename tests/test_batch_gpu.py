@@ -59,6 +59,59 @@ def test_batch_bitwise_equals_single(torch, lat, precision, cfg):
         lbm.lbm_batch_destroy(b)
 
 
+@pytest.mark.parametrize("lat", [0, 1])
+@pytest.mark.parametrize("bx,fo,graph", [(64, 2, 0), (128, 0, 4), (256, 2, 0), (128, 1, 0)])
+def test_staged_batch_bitwise_equals_single(torch, lat, bx, fo, graph):
+    """The halo-staged batch kernel (cp.async prefetch of the next tile)
+    against each grid stepped alone by the plain step kernel."""
+    stream = torch.cuda.Stream()
+    ws = mixed_grids(1, lat)
+    if fo != 2:
+        ws = [dict(w, force_order=fo) for w in ws]
+    members = [lbm.Sim(w, stream=stream.cuda_stream).init() for w in ws]
+    alone = [lbm.Sim(w).init() for w in ws]
+    b = lbm.lbm_batch_create(lat, 1, fo, stream.cuda_stream, 16)
+    try:
+        for m in members:
+            lbm.lbm_batch_add(b, m.ctx)
+        lbm.lbm_batch_set_config(b, bx, 1, graph)
+        lbm.lbm_batch_set_staging(b, 1)
+        assert lbm.lbm_batch_get_staging(b) == 1
+        lbm.lbm_batch_step(b, 7)
+        lbm.lbm_batch_step(b, 10)
+        for a in alone:
+            a.step(17)
+        for m, a in zip(members, alone):
+            np.testing.assert_array_equal(m.get_state(), a.get_state())
+    finally:
+        lbm.lbm_batch_destroy(b)
+
+
+def test_staging_rules(torch):
+    stream = torch.cuda.Stream()
+    b16 = lbm.lbm_batch_create(0, 2, 2, stream.cuda_stream, 2)
+    b32 = lbm.lbm_batch_create(0, 1, 2, stream.cuda_stream, 2)
+    try:
+        with pytest.raises(lbm.LbmError) as ei:   # FP16-scaled: 2-byte populations
+            lbm.lbm_batch_set_staging(b16, 1)
+        assert ei.value.status == lbm.LBM_EINVAL
+        lbm.lbm_batch_set_config(b32, 128, 2, 0)
+        with pytest.raises(lbm.LbmError):         # two sites per thread
+            lbm.lbm_batch_set_staging(b32, 1)
+        lbm.lbm_batch_set_config(b32, 128, 1, 0)
+        lbm.lbm_batch_set_staging(b32, 1)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_set_config(b32, 128, 2, 0)
+        assert lbm.lbm_batch_get_config(b32)[:2] == (128, 1)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_set_staging(b32, 2)
+        lbm.lbm_batch_set_staging(b32, 0)
+        assert lbm.lbm_batch_get_staging(b32) == 0
+    finally:
+        lbm.lbm_batch_destroy(b16)
+        lbm.lbm_batch_destroy(b32)
+
+
 def test_batch_membership_rules(torch):
     stream = torch.cuda.Stream()
     ws = mixed_grids(1)
@@ -106,7 +159,8 @@ def test_batch_tune_then_continue(torch):
         assert bx in (64, 128, 256) and spt in (1, 2)
         assert lbm.lbm_batch_get_config(b)[:2] == (bx, spt)
         n_tuned = lbm.lbm_step_count(members[0].ctx)
-        assert n_tuned == 6 * (4 + 2)
+        assert n_tuned == 9 * (4 + 2)  # 6 plain candidates + 3 halo-staged ones
+        assert lbm.lbm_batch_get_staging(b) in (0, 1)
         lbm.lbm_batch_step(b, 5)
         for a in alone:
             a.step(n_tuned + 5)
