@@ -351,6 +351,7 @@ def extra_ragged(lbm, torch, W, peak, single_mlups, K=5, inner=10):
         for s_ in sims:
             lbm.lbm_batch_add(b, s_.ctx)
         bx, spt = lbm.lbm_batch_tune(b, 4)
+        staged = lbm.lbm_batch_get_staging(b)
         lbm.lbm_batch_set_config(b, bx, spt, inner)
         lbm.lbm_batch_step(b, 2 * inner)
         t = event_time(torch, stream, lambda: lbm.lbm_batch_step(b, inner), K)
@@ -362,7 +363,7 @@ def extra_ragged(lbm, torch, W, peak, single_mlups, K=5, inner=10):
     mlups = sites * inner * K / t / 1e6
     return {"workload": "ragged_batch_64_d2q37_fp32", "grids": len(ws), "sites": sites,
             "mlups": mlups, "roofline_frac": mlups * 1e6 * 296 / (peak * 1e9),
-            "tuned": {"block_x": bx, "sites_per_thread": spt, "graph_steps": inner},
+            "tuned": {"block_x": bx, "sites_per_thread": spt, "halo_staged": staged, "graph_steps": inner},
             "vs_single_grid_mlups": mlups / single_mlups}
 
 

@@ -11,6 +11,10 @@ Measured on GB300 (the numbers the bounds below guard):
   The FP32 u and q errors lie ~100x above the storage floor: the float
   arithmetic of the collision, not the storage, limits FP32 at this length
   (a stable flow: the butterfly floor stays at 1e-13).
+  D3Q39 Rayleigh-Benard 512 x 512 x 256, FP16-scaled, 10k steps:
+    1,000 steps   rho 5.8e-6  u 9.3e-4  T 4.6e-6  q 9.6e-3  (floor: 5.6e-6 9.2e-4 4.5e-6 9.6e-3)
+    10,000 steps  rho 4.7e-5  u 3.0e-3  T 5.1e-5  q 1.5e-2
+  FP16 sits on its storage floor: 11 bits per scaled deviation.
 """
 import os
 import tempfile
@@ -87,3 +91,19 @@ def test_rb2d_fp32_full_length_accuracy():
     assert r["codec"]["rho"] <= 1e-6 and r["codec"]["T"] <= 1e-6
     # u and q: the FP32 arithmetic floor, guarded at about twice the measured value
     assert r["codec"]["u"] <= 5e-5 and r["codec"]["q"] <= 2e-4, r["codec"]
+
+
+def test_rb3d_fp16_full_length_accuracy():
+    """D3Q39 Rayleigh-Benard 512 x 512 x 256, FP16-scaled, the full 10k steps
+    against the float-float FP64 step (which agrees with IEEE double to
+    ~1e-12 over this length and runs twice as fast)."""
+    import torch
+    w, prec = A.workload("rb3d")
+    s = torch.cuda.Stream()
+    res = A.codec_accuracy(w, prec, [1000, 10000], stream=s.cuda_stream, runs=("codec",),
+                           ref_arith=lbm.LBM_ARITH_FLOAT_PAIR)
+    r1, r10 = res[1000]["codec"], res[10000]["codec"]
+    assert r1["rho"] <= 1e-5 and r1["T"] <= 1e-5 and r1["u"] <= 2e-3 and r1["q"] <= 2e-2, r1
+    assert r10["rho"] <= 1e-4 and r10["T"] <= 1e-4, r10
+    # u and q: the FP16 storage floor, guarded at about twice the measured value
+    assert r10["u"] <= 6e-3 and r10["q"] <= 3e-2, r10
