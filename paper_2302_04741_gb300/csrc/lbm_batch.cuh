@@ -75,12 +75,13 @@ __global__ void __launch_bounds__(256, min_blocks<L, P>())
       if (site >= p.N) continue;
       const int x = site % p.nx, row = site / p.nx;
       const int y = row % p.ny, z = row / p.ny;
+      constexpr bool SC = scaled_step<P, FO>();
       R d[L::Q];
-      if (interior) pull_interior<L, P, R, LD_RO>(fin + site, p, y, z, d);
-      else pull<L, P, R, LD_RO>(fin, p, x, y, z, d);
+      if (interior) pull_interior<L, P, R, LD_RO, SC>(fin + site, p, y, z, d);
+      else pull<L, P, R, LD_RO, SC>(fin, p, x, y, z, d);
       R g[3];
       site_force_r<L::D, R>(p, x, y, z, site, g);
-      collide_store<L, P, FO>(d, g, site, fout, p);
+      collide_store<L, P, FO, SC>(d, g, site, fout, p);
     }
   }
 }

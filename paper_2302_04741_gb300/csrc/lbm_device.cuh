@@ -302,6 +302,36 @@ template <> struct Codec<P_FP16S> {
   __device__ __forceinline__ static T load_cg(const T* p) { return __ldcg(p); }
 };
 
+// Working representation of the step kernels.  An FP16-scaled step collides
+// the stored value itself, h_i = s (f_i - w_i) / w_i, instead of the deviation
+// d_i = w_i h_i / s: Eq. lbm divided by w_i / s reads
+//   h*_i = (1 - om) h_i + s [om drho + rho (om p_i + (1 - om/2) F'_i)],
+// since the pair weights cancel, so the decode multiply, the weight multiply
+// of the equilibrium and the encode multiply of every population drop out;
+// s, a power of two, scales the handful of per-site coefficients exactly.
+// The sigma-bar force order (FO 3) keeps deviations (its stress tensor is a
+// sum over them).
+template <int P, int FO>
+__host__ __device__ constexpr bool scaled_step() {
+  return P == P_FP16S && FO != 3;
+}
+template <class L, int P, int I, bool SC>
+__device__ __forceinline__ typename Codec<P>::R step_in(typename Codec<P>::T v, const StepParams& p) {
+  if constexpr (SC) return __half2float(v);
+  else return Codec<P>::template decode<L, I>(v, p);
+}
+// a deviation formed in the kernel (a wall slot) in the working representation
+template <int I, bool SC, class R>
+__device__ __forceinline__ R step_from_dev(R d, const StepParams& p) {
+  if constexpr (SC) return d * R(p.h_enc[I]);
+  else return d;
+}
+template <class L, int P, int I, bool SC>
+__device__ __forceinline__ typename Codec<P>::T step_out(typename Codec<P>::R x, const StepParams& p) {
+  if constexpr (SC) return __float2half_rn(x);
+  else return Codec<P>::template encode<L, I>(x, p);
+}
+
 // The FP16 factors of a lattice for the scale in p (host side).  Both are
 // products of two floats, as the device formed them before they became
 // parameters, so the stored values are unchanged.
@@ -421,6 +451,33 @@ __device__ __forceinline__ RawMoments<L, R> raw_moments(const R (&d)[L::Q]) {
   r.drho = drho;
   r.j[0] = j0; r.j[1] = j1; r.j[2] = j2;
   r.k2 = k2;
+  return r;
+}
+
+// The same sums from the scaled values h_i = s d_i / w_i of an FP16-scaled
+// step: each pair is weighted by its common w_i, and 1/s (a power of two)
+// applied once to each sum.
+template <class L, class R>
+__device__ __forceinline__ RawMoments<L, R> raw_moments_scaled(const R (&h)[L::Q], R inv_s) {
+  constexpr int Q = L::Q, D = L::D, NP = (Q - 1) / 2;
+  RawMoments<L, R> r;
+  R drho = h[0] * R(float(L::W(0))), j0 = R(0), j1 = R(0), j2 = R(0), k2 = R(0);
+  static_for<0, NP>([&](auto K) {
+    constexpr int ip = 2 * K + 1, im = ip + 1;
+    constexpr int ex = L::E(ip, 0), ey = L::E(ip, 1), ez = L::E(ip, 2);
+    constexpr int e2 = ex * ex + ey * ey + ez * ez;
+    constexpr double w = L::W(ip);
+    const R s = h[ip] + h[im];
+    const R a = h[ip] - h[im];
+    drho = fma(s, R(float(w)), drho);
+    if constexpr (ex != 0) j0 = fma(a, R(float(ex * w)), j0);
+    if constexpr (ey != 0) j1 = fma(a, R(float(ey * w)), j1);
+    if constexpr (D == 3 && ez != 0) j2 = fma(a, R(float(ez * w)), j2);
+    k2 = fma(s, R(float(e2 * w)), k2);
+  });
+  r.drho = drho * inv_s;
+  r.j[0] = j0 * inv_s; r.j[1] = j1 * inv_s; r.j[2] = j2 * inv_s;
+  r.k2 = k2 * inv_s;
   return r;
 }
 

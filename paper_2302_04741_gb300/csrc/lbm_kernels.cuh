@@ -62,8 +62,9 @@ __device__ __forceinline__ void site_force_r(const StepParams& p, int x, int y, 
 }
 
 // Pull of all Q populations of site (x, y, z) with the boundary rules, decoded
-// to deviations in type RR.  The wall axis is the last axis (y in 2-D, z in 3-D).
-template <class L, int P, class RR, int LD = LD_HINT>
+// to deviations in type RR (SC: the scaled values of an FP16-scaled step, see
+// scaled_step).  The wall axis is the last axis (y in 2-D, z in 3-D).
+template <class L, int P, class RR, int LD = LD_HINT, bool SC = false>
 __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fin,
                                      const StepParams& p, int x, int y, int z, RR (&d)[L::Q]) {
   using C = Codec<P>;
@@ -85,7 +86,7 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
       constexpr int i = I;
       constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
       const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
-      d[i] = RR(C::template decode<L, i>(ldpop<C, LD>(fin + i * N + off, p), p));
+      d[i] = RR(step_in<L, P, i, SC>(ldpop<C, LD>(fin + i * N + off, p), p));
     });
     return;
   }
@@ -118,13 +119,14 @@ __device__ __forceinline__ void pull(const typename Codec<P>::T* __restrict__ fi
     const int sA = a - eA;
     if (sA >= 0 && sA < nA) {
       const int off = zs[ez + 3] + ys[ey + 3] + xs[ex + 3];
-      d[i] = RR(C::template decode<L, i>(ldpop<C, LD>(fin + i * N + off, p), p));
+      d[i] = RR(step_in<L, P, i, SC>(ldpop<C, LD>(fin + i * N + off, p), p));
     } else if (p.wall == W_BOUNCE) {
+      // d_i = d_io and w_i = w_io: the scaled values agree as well
       constexpr int io = opposite<i>();
       const int mA = side == 0 ? eA - 1 - a : 2 * nA - 1 - sA;
-      d[i] = RR(C::template decode<L, io>(ldpop<C, LD>(fin + io * N + colbase + mA * lineA, p), p));
+      d[i] = RR(step_in<L, P, io, SC>(ldpop<C, LD>(fin + io * N + colbase + mA * lineA, p), p));
     } else {
-      d[i] = fma(rm1, RR(p.fw[side][i]), RR(p.fwd[side][i]));
+      d[i] = step_from_dev<i, SC>(fma(rm1, RR(p.fw[side][i]), RR(p.fwd[side][i])), p);
     }
   });
 }
@@ -197,7 +199,7 @@ __device__ __forceinline__ void pull_solid(const typename Codec<P>::T* __restric
 // source offset relative to the thread's own site, i*N + (row / plane shift)
 // - e_ix, is the same for the whole block (rows wrap only through the block's
 // y, z), so addresses are a per-thread base plus block-uniform offsets.
-template <class L, int P, class RR, int LD = LD_HINT>
+template <class L, int P, class RR, int LD = LD_HINT, bool SC = false>
 __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __restrict__ fsite,
                                               const StepParams& p, int y, int z,
                                               RR (&d)[L::Q]) {
@@ -214,7 +216,7 @@ __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __rest
     constexpr int i = I;
     constexpr int ex = L::E(i, 0), ey = L::E(i, 1), ez = L::E(i, 2);
     const long long off = i * N + dz[ez + 3] + dy[ey + 3] - ex;
-    d[i] = RR(C::template decode<L, i>(ldpop<C, LD>(fsite + off, p), p));
+    d[i] = RR(step_in<L, P, i, SC>(ldpop<C, LD>(fsite + off, p), p));
   });
 }
 
@@ -234,7 +236,9 @@ __device__ __forceinline__ void pull_interior(const typename Codec<P>::T* __rest
 // drop terms).  Each pair is stored as even +- odd: the even part (density,
 // temperature) is shared by e and -e, so its rounding cancels in the odd part
 // that carries the momentum; only the final rounding of each member remains.
-template <class L, int P, int FO>
+// SC (scaled_step): d holds h_i = s d_i / w_i, and every coefficient that
+// multiplies w_i above is carried times s instead (exact: s is a power of two).
+template <class L, int P, int FO, bool SC = false>
 __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
                                               const typename Codec<P>::R (&g)[3], int site,
                                               typename Codec<P>::T* __restrict__ fout,
@@ -243,8 +247,14 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   using R = typename C::R;
   constexpr int NP = (L::Q - 1) / 2, NS = L::NSHELL, D = L::D;
   constexpr bool EX = P != P_FP16S;  // quadrature constants as hi + lo pairs
+  static_assert(!SC || scaled_step<P, FO>(), "scaled values: FP16-scaled storage, FO 0..2");
   const size_t N = (size_t)p.N;
-  const RawMoments<L, R> r = raw_moments<L, R>(d);
+  const RawMoments<L, R> r = SC ? raw_moments_scaled<L, R>(d, R(p.h_inv_scale)) : raw_moments<L, R>(d);
+  // times s: the coefficients of w_i in the scaled representation
+  auto scl = [&](R v) {
+    if constexpr (SC) return v * R(p.h_scale);
+    else return v;
+  };
   // mid-point state (R1): rho, u = u~ + g/2, theta
   const R rho = R(1) + r.drho;
   const R irho = R(1) / rho;
@@ -260,12 +270,14 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   const R om1 = R(1) - om;
   const R hom1 = R(0.5) * om1;
   const R kf = R(1) - R(0.5) * om;
-  const R rom = rho * om;
-  const R rkgu = FO >= 1 ? rho * kf * gu : R(0);
+  const R rom0 = rho * om;
+  const R rom = scl(rom0);
+  const R rkgu = scl(FO >= 1 ? rho * kf * gu : R(0));
+  const R rkf = scl(rho * kf);
   R cu[3], cs[3];
   for (int a = 0; a < 3; ++a) {
     cu[a] = mul_c<L, R, EX>(u[a]);
-    cs[a] = mul_c<L, R, EX>(rho * kf * g[a]);
+    cs[a] = mul_c<L, R, EX>(rkf * g[a]);
   }
   // per-shell coefficients as polynomials in tx = Th |xi|^2 (constant hi + lo)
   //   A0 = a00 + tx (c1 + tx / 8 [NEQ 4]),  A1 = b0 + tx / 2,  A2 = g0 + tx / 4 [NEQ 4]
@@ -280,12 +292,12 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   c1 *= Th;  // A0 = a00 + c1 X2 + Th^2 X2^2 / 8 = a00 + (c1 / Th) tx + tx^2 / 8
   const R b0 = R(1) - R(0.5) * u2 - R(0.5 * (D + 2)) * Th;
   R P0[NS], P2[NS], Q1[NS], A1[NS];
-  const R base = om * r.drho - rkgu;
+  const R base = scl(om * r.drho) - rkgu;
   // rho om multiplies every direction's equilibrium part at this site, so its
   // rounding would act as a common factor (a coherent momentum / energy error
   // per step): carry it as rom + rom_lo, with the exact FMA residual (in
   // double the product's rounding is far below the tolerances: rom_lo = 0).
-  const R rom_lo = sizeof(R) == sizeof(double) ? R(0) : fma(rho, om, -rom);
+  const R rom_lo = sizeof(R) == sizeof(double) ? R(0) : scl(fma(rho, om, -rom0));
   static_for<0, NS>([&](auto S) {
     constexpr int sh = S;
     constexpr double X2d = L::c2 * double(L::E2(sh));
@@ -319,10 +331,10 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
   // FP64 storage probe: the stored deviation rounded as a float codec stores it
   const bool probe = P == P_FP64 && p.storage_probe != 0;
   {
-    R d0 = fma(d[0], om1, mul_w<L, 0, R, EX>(P0[0]));
+    R d0 = fma(d[0], om1, SC ? P0[0] : mul_w<L, 0, R, EX>(P0[0]));
     if constexpr (P == P_FP64)
       if (probe) d0 = probe_round<0>(d0, p);
-    fo[0] = C::template encode<L, 0>(d0, p);
+    fo[0] = step_out<L, P, 0, SC>(d0, p);
   }
   static_for<0, NP>([&](auto K) {
     constexpr int ip = 2 * K + 1, im = ip + 1;
@@ -339,8 +351,8 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
       od_in = od_in + edot<L, ip>(cs);
     }
     if constexpr (FO == 3) od_in += stress_pair<L, ip, R>(st);
-    const R ev = fma(d[ip] + d[im], hom1, mul_w<L, ip, R, EX>(ev_in));
-    const R od = fma(d[ip] - d[im], hom1, mul_w<L, ip, R, EX>(od_in));
+    const R ev = fma(d[ip] + d[im], hom1, SC ? ev_in : mul_w<L, ip, R, EX>(ev_in));
+    const R od = fma(d[ip] - d[im], hom1, SC ? od_in : mul_w<L, ip, R, EX>(od_in));
     R dp = ev + od, dm = ev - od;
     if constexpr (P == P_FP64) {
       if (probe) {
@@ -348,8 +360,8 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
         dm = probe_round<im>(dm, p);
       }
     }
-    fo[ip * N] = C::template encode<L, ip>(dp, p);
-    fo[im * N] = C::template encode<L, im>(dm, p);
+    fo[ip * N] = step_out<L, P, ip, SC>(dp, p);
+    fo[im * N] = step_out<L, P, im, SC>(dm, p);
   });
 }
 
@@ -373,11 +385,20 @@ __device__ __forceinline__ void collide_store(typename Codec<P>::R (&d)[L::Q],
 #ifndef LBM_DF_BLOCKS
 #define LBM_DF_BLOCKS 2
 #endif
+// LBM_HALF_D2Q37_BLOCKS, LBM_HALF_D3Q39_BLOCKS: the same for FP16-scaled
+// storage (whose 2-byte loads bring half the bytes per load instruction).
+#ifndef LBM_HALF_D2Q37_BLOCKS
+#define LBM_HALF_D2Q37_BLOCKS LBM_FLOAT_D2Q37_BLOCKS
+#endif
+#ifndef LBM_HALF_D3Q39_BLOCKS
+#define LBM_HALF_D3Q39_BLOCKS LBM_FLOAT_D3Q39_BLOCKS
+#endif
 template <class L, int P>
 constexpr int min_blocks() {
-  return P == P_FP64 ? 1
-                     : (P == P_FP64DF ? LBM_DF_BLOCKS
-                                      : (L::Q > 37 ? LBM_FLOAT_D3Q39_BLOCKS : LBM_FLOAT_D2Q37_BLOCKS));
+  return P == P_FP64     ? 1
+         : P == P_FP64DF ? LBM_DF_BLOCKS
+         : P == P_FP16S  ? (L::Q > 37 ? LBM_HALF_D3Q39_BLOCKS : LBM_HALF_D2Q37_BLOCKS)
+                         : (L::Q > 37 ? LBM_FLOAT_D3Q39_BLOCKS : LBM_FLOAT_D2Q37_BLOCKS);
 }
 
 // Line of the wall axis a block works on.  With walls, the six wall rows
@@ -425,10 +446,11 @@ __global__ void __launch_bounds__(256, min_blocks<L, P>())
   R g[3];
   site_force_r<L::D, R>(p, x, y, z, site, g);
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  constexpr bool SC = scaled_step<P, FO>();
   R d[L::Q];
-  if (interior) pull_interior<L, P, R>(fin + site, p, y, z, d);
-  else pull<L, P, R>(fin, p, x, y, z, d);
-  collide_store<L, P, FO>(d, g, site, fout, p);
+  if (interior) pull_interior<L, P, R, LD_HINT, SC>(fin + site, p, y, z, d);
+  else pull<L, P, R, LD_HINT, SC>(fin, p, x, y, z, d);
+  collide_store<L, P, FO, SC>(d, g, site, fout, p);
 }
 
 // ------------------------------------------------------------ init

@@ -102,7 +102,7 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
 
 // ----------------------------------------------------- staged pull of one site
 // stage: the tile's shared-memory stage; x0: first site of the tile.
-template <class L, int P, class R>
+template <class L, int P, class R, bool SC>
 __device__ __forceinline__ void pull_staged(const unsigned char* stage,
                                             const typename Codec<P>::T* __restrict__ fin,
                                             const StepParams& p, int x0, int x, int y, int z,
@@ -119,7 +119,7 @@ __device__ __forceinline__ void pull_staged(const unsigned char* stage,
     static_for<0, Q>([&](auto I) {
       constexpr int i = I;
       constexpr int ex = L::E(i, 0);
-      d[i] = R(C::template decode<L, i>(sb[i * G::ROW_ELEMS - ex], p));
+      d[i] = R(step_in<L, P, i, SC>(sb[i * G::ROW_ELEMS - ex], p));
     });
     return;
   }
@@ -155,19 +155,19 @@ __device__ __forceinline__ void pull_staged(const unsigned char* stage,
     if (!near || (sA >= 0 && sA < nA)) {
       const int xs = x - ex;
       if (xs >= 0 && xs < nx) {
-        d[i] = R(C::template decode<L, i>(sb[i * G::ROW_ELEMS - ex], p));
+        d[i] = R(step_in<L, P, i, SC>(sb[i * G::ROW_ELEMS - ex], p));
       } else {
         const int sx = wrap3(xs, nx);
         const int sy = wrap3(y - ey, ny);
         const int sz = D == 3 ? wrap3(z - ez, nz) : 0;
-        d[i] = R(C::template decode<L, i>(C::load(fin + i * N + (sz * ny + sy) * nx + sx, p), p));
+        d[i] = R(step_in<L, P, i, SC>(C::load(fin + i * N + (sz * ny + sy) * nx + sx, p), p));
       }
     } else if (p.wall == W_BOUNCE) {
       constexpr int io = opposite<i>();
       const int mA = side == 0 ? eA - 1 - a : 2 * nA - 1 - sA;
-      d[i] = R(C::template decode<L, io>(C::load(fin + io * N + colbase + mA * lineA, p), p));
+      d[i] = R(step_in<L, P, io, SC>(C::load(fin + io * N + colbase + mA * lineA, p), p));
     } else {
-      d[i] = fma(rm1, R(p.fw[side][i]), R(p.fwd[side][i]));
+      d[i] = step_from_dev<i, SC>(fma(rm1, R(p.fw[side][i]), R(p.fwd[side][i])), p);
     }
   });
 }
@@ -261,14 +261,15 @@ __global__ void __launch_bounds__(TMA_THREADS, 3) k_step_tma(const __grid_consta
     const bool warp_edge = wx0 < 3 || wx0 + 31 >= p.nx - 3;
     const bool active = x < p.nx;
     R d[Q];
-    if (active) pull_staged<L, P, R>(smem + (size_t)s * SB, fin, p, x0, x, y, z, warp_edge, d);
+    constexpr bool SC = scaled_step<P, FO>();
+    if (active) pull_staged<L, P, R, SC>(smem + (size_t)s * SB, fin, p, x0, x, y, z, warp_edge, d);
     __syncwarp();
     if (lane == 0) mbar_arrive(empty0 + 8 * s);
     if (active) {
       const int site = (z * p.ny + y) * p.nx + x;
       R g[3];
       site_force_r<D, R>(p, x, y, z, site, g);
-      collide_store<L, P, FO>(d, g, site, fout, p);
+      collide_store<L, P, FO, SC>(d, g, site, fout, p);
     }
   }
 }

@@ -119,10 +119,11 @@ __global__ void __launch_bounds__(WAVE_BX, wave_min_blocks<L, P>())
       const bool interior = !near && wx0 >= 3 && wx0 + 31 <= p.nx - 4;
       R g[3];
       site_force_r<D, R>(p, x, y, z, site, g);
+      constexpr bool SC = scaled_step<P, FO>();
       R d[L::Q];
-      if (interior) pull_interior<L, P, R, LD_CG>(fin + site, p, y, z, d);
-      else pull<L, P, R, LD_CG>(fin, p, x, y, z, d);
-      collide_store<L, P, FO>(d, g, site, fout, p);
+      if (interior) pull_interior<L, P, R, LD_CG, SC>(fin + site, p, y, z, d);
+      else pull<L, P, R, LD_CG, SC>(fin, p, x, y, z, d);
+      collide_store<L, P, FO, SC>(d, g, site, fout, p);
     }
     __threadfence();
     __syncthreads();
