@@ -9,7 +9,11 @@
 // one operation here; flop rates are twice that for FMAs).
 //
 // kinds: 0 DFMA, 1 DADD, 2 FFMA, 3 double -> float conversion,
-//        4 float -> double conversion, 5 integer add (32-bit)
+//        4 float -> double conversion, 5 integer add (32-bit),
+//        6 packed FFMA (fma.rn.f32x2: two FMAs per instruction, counted as
+//        two operations), 7 float -> half -> float round trips (two
+//        conversions per step)
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -76,6 +80,37 @@ __global__ void __launch_bounds__(256) k_iadd(double* out, int a) {
   if (s == 12345678) out[0] = s;
 }
 
+__global__ void __launch_bounds__(256) k_ffma2(double* out, float a, float b) {
+  unsigned long long x[kAcc], av, bv;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(av) : "f"(a));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(bv) : "f"(b));
+  for (int k = 0; k < kAcc; ++k) {
+    const float lo = threadIdx.x * 1e-6f + k, hi = lo + 0.5f;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x[k]) : "f"(lo), "f"(hi));
+  }
+  for (int it = 0; it < kIters; ++it)
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[k]) : "l"(av), "l"(bv));
+  float s = 0.f;
+  for (int k = 0; k < kAcc; ++k) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[k]));
+    s += lo + hi;
+  }
+  if (s == 12345.678f) out[0] = s;
+}
+
+__global__ void __launch_bounds__(256) k_half(double* out, float a) {
+  float x[kAcc];
+  for (int k = 0; k < kAcc; ++k) x[k] = threadIdx.x * 1e-6f + k + a;
+  for (int it = 0; it < kIters; ++it)
+#pragma unroll
+    for (int k = 0; k < kAcc; ++k) x[k] = __half2float(__float2half_rn(x[k])) + a;
+  float s = 0.f;
+  for (int k = 0; k < kAcc; ++k) s += x[k];
+  if (s == 12345.678f) out[0] = s;
+}
+
 }  // namespace
 
 // Operations per second of probe `kind` on the current device (reps timed
@@ -94,6 +129,8 @@ extern "C" double alu_probe(int kind, int reps) {
       case 1: k_dadd<<<grid, block>>>(out, 1e-7); break;
       case 2: k_ffma<<<grid, block>>>(out, 0.9999f, 1e-4f); break;
       case 3: case 4: k_cvt<<<grid, block>>>(out, 0.25); break;
+      case 6: k_ffma2<<<grid, block>>>(out, 0.9999f, 1e-4f); break;
+      case 7: k_half<<<grid, block>>>(out, 0.25f); break;
       default: k_iadd<<<grid, block>>>(out, 12345); break;
     }
   };
@@ -113,5 +150,6 @@ extern "C" double alu_probe(int kind, int reps) {
   cudaFree(out);
   if (!ok || ms <= 0.f) return 0.0;
   const double per_launch = (double)grid.x * block.x * kAcc * kIters * (kind >= 3 ? 2.0 : 1.0);
+  // (kind 7 also adds one FADD per step, which is not counted)
   return per_launch * reps / (ms * 1e-3);
 }

@@ -12,7 +12,8 @@ from paper_2302_04741_gb300 import build as B
 
 LIB = os.path.join(B.BUILD, "libalu_peaks.so")
 SRC = os.path.join(B.CSRC, "alu_peaks.cu")
-KINDS = {"dfma": 0, "dadd": 1, "ffma": 2, "f64_f32_convert": 3, "int32": 5}
+KINDS = {"dfma": 0, "dadd": 1, "ffma": 2, "f64_f32_convert": 3, "int32": 5, "ffma_packed_f32x2": 6,
+         "f32_f16_convert": 7}
 
 
 def build():
