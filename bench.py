@@ -590,6 +590,23 @@ def run_ours(args):
     e2e = {"value": world * N * inner * Ke / (e2e_ms / 1e3) / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 4 * N * 8, "d2h_bytes_per_step": 6 * N * 8,
            "step": f"lbm_init(pinned host rho,u,T) + lbm_step({inner}) + lbm_moments(pinned host)"}
+    # the read-out kernel alone, into device memory (k_moments: Q float
+    # populations in, rho, u, T, q as doubles out)
+    d_out = [torch.empty(n, dtype=torch.float64, device="cuda") for n in (N, 2 * N, N, 2 * N)]
+    ptrs = [t.data_ptr() for t in d_out]
+    lbm.lbm_moments_async(e2e_sim.ctx, *ptrs)
+    Km = 20
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Km):
+        lbm.lbm_moments_async(e2e_sim.ctx, *ptrs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mom_us = e0.elapsed_time(e1) * 1e3 / Km
+    mom_bytes = N * (37 * 4 + 6 * 8)
+    e2e["k_moments_device"] = {"us": mom_us, "bytes": mom_bytes,
+                               "hbm_frac": mom_bytes / (mom_us * 1e-6) / (peak * 1e9),
+                               "note": "lbm_moments_async into device memory, 20 launches, CUDA events"}
     e2e_sim.close()
 
     configs = {}

@@ -2,6 +2,7 @@
 small launch sequence of the step kernel).
 
     python -m paper_2302_04741_gb300.run_steps --config rb2d --precision fp64 --steps 3
+    python -m paper_2302_04741_gb300.run_steps --config rb2d --precision fp32 --steps 3 --moments 20
 """
 import argparse
 
@@ -28,6 +29,8 @@ def main():
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
     ap.add_argument("--arith", type=int, default=None, help="lbm_options.fp64_arith (FP64 storage)")
+    ap.add_argument("--moments", type=int, default=0,
+                    help="then K read-outs into device memory (lbm_moments_async), timed with CUDA events")
     args = ap.parse_args()
     import torch
     import paper_2302_04741_gb300 as lbm
@@ -40,6 +43,26 @@ def main():
     torch.cuda.synchronize()
     st = sim.conserved()
     print("ok", args.config, args.precision, args.steps, "mass", st[1])
+    if args.moments > 0:
+        D, N = sim.D, sim.N
+        rho = torch.empty(N, dtype=torch.float64, device="cuda")
+        u = torch.empty(D * N, dtype=torch.float64, device="cuda")
+        T = torch.empty(N, dtype=torch.float64, device="cuda")
+        q = torch.empty(D * N, dtype=torch.float64, device="cuda")
+        out = [t.data_ptr() for t in (rho, u, T, q)]
+        stream = torch.cuda.current_stream()
+        lbm.lbm_moments_async(sim.ctx, *out)  # warm-up (the context's stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.moments):
+            lbm.lbm_moments_async(sim.ctx, *out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / args.moments
+        elem = {W.FP64: 8, W.FP32_SHIFTED: 4, W.FP16_SCALED: 2}[PRECISIONS[args.precision]]
+        nbytes = N * (sim.Q * elem + (2 + 2 * D) * 8)
+        print(f"moments {args.moments} x {us:.2f} us per read-out, {nbytes / us / 1e3:.1f} GB/s algorithmic")
     sim.close()
 
 
