@@ -593,13 +593,12 @@ def run_ours(args):
     # the read-out kernel alone, into device memory (k_moments: Q float
     # populations in, rho, u, T, q as doubles out)
     d_out = [torch.empty(n, dtype=torch.float64, device="cuda") for n in (N, 2 * N, N, 2 * N)]
-    ptrs = [t.data_ptr() for t in d_out]
-    lbm.lbm_moments_async(e2e_sim.ctx, *ptrs)
+    lbm.lbm_moments_async(e2e_sim.ctx, *d_out)
     Km = 20
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(Km):
-        lbm.lbm_moments_async(e2e_sim.ctx, *ptrs)
+        lbm.lbm_moments_async(e2e_sim.ctx, *d_out)
     e1.record(stream)
     torch.cuda.synchronize()
     mom_us = e0.elapsed_time(e1) * 1e3 / Km

@@ -49,7 +49,7 @@ def main():
         u = torch.empty(D * N, dtype=torch.float64, device="cuda")
         T = torch.empty(N, dtype=torch.float64, device="cuda")
         q = torch.empty(D * N, dtype=torch.float64, device="cuda")
-        out = [t.data_ptr() for t in (rho, u, T, q)]
+        out = (rho, u, T, q)
         stream = torch.cuda.current_stream()
         lbm.lbm_moments_async(sim.ctx, *out)  # warm-up (the context's stream)
         torch.cuda.synchronize()
