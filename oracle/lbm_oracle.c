@@ -42,9 +42,10 @@
  *       the same slots with rho_w f0_i(1, 0, T_wall) where rho_w makes the
  *       column's incoming mass equal its outgoing mass.  Pinned by mass
  *       conservation, the conduction profile, Fourier's law, the no-slip
- *       channel parabola and the kinetic slip; the exact slot values in the
- *       first rows are parity unpinned (only a loop restatement of this
- *       reading checks them), as for R15.
+ *       channel parabola and the kinetic slip; at slot level by the
+ *       micro-reversibility of streaming with bounce-back and by the closed
+ *       form of the thermal wall's refill of a resting fluid (as for R15's
+ *       solid sites; tests/test_wall_pins.py).
  *   R11 storage holds the post-collision distribution f*; a step pulls
  *       f~_i(x) = f*_i(x - e_i) and collides.  init places f~ = f0 - F/2 at
  *       the slots the first pull reads, so the pulled state at t = 0 is
