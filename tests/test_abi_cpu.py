@@ -111,3 +111,14 @@ def test_library_tables_are_gauss_hermite(libpath, lat, deg):
         for a in alpha:
             exact = 0 if a % 2 else exact * int(np.prod(np.arange(a - 1, 0, -2)) if a else 1)
         assert abs(s - exact) < 2e-14 * max(1, exact)
+
+
+def test_batch_entry_points_reject_a_null_batch(libpath):
+    """Argument checks that precede any CUDA call (no GPU needed)."""
+    calls = [lambda: lbm.lbm_batch_set_staging(None, 1), lambda: lbm.lbm_batch_get_staging(None),
+             lambda: lbm.lbm_batch_set_config(None, 128, 1, 0), lambda: lbm.lbm_batch_get_config(None),
+             lambda: lbm.lbm_batch_step(None, 1), lambda: lbm.lbm_batch_tune(None, 4)]
+    for call in calls:
+        with pytest.raises(lbm.LbmError) as ei:
+            call()
+        assert ei.value.status == lbm.LBM_EINVAL
