@@ -93,17 +93,23 @@ def test_rb2d_fp32_full_length_accuracy():
     assert r["codec"]["u"] <= 5e-5 and r["codec"]["q"] <= 2e-4, r["codec"]
 
 
-def test_rb3d_fp16_full_length_accuracy():
-    """D3Q39 Rayleigh-Benard 512 x 512 x 256, FP16-scaled, the full 10k steps
-    against the float-float FP64 step (which agrees with IEEE double to
-    ~1e-12 over this length and runs twice as fast)."""
+def test_rb3d_fp16_full_size_accuracy():
+    """D3Q39 Rayleigh-Benard 512 x 512 x 256, FP16-scaled, against the
+    float-float FP64 step (which agrees with IEEE double to ~1e-12 over this
+    length): 1,000 steps, and at 100 steps the codec's error against its
+    storage floor.  The full 10,000-step run is the committed command
+    `python -m paper_2302_04741_gb300.accuracy rb3d --steps 10000
+    --checkpoints 1000 5000 --runs codec --ref-arith 1` (about six minutes on
+    GB300), whose result is the table in the module docstring."""
     import torch
     w, prec = A.workload("rb3d")
     s = torch.cuda.Stream()
-    res = A.codec_accuracy(w, prec, [1000, 10000], stream=s.cuda_stream, runs=("codec",),
+    res = A.codec_accuracy(w, prec, [1000], stream=s.cuda_stream, runs=("codec",),
                            ref_arith=lbm.LBM_ARITH_FLOAT_PAIR)
-    r1, r10 = res[1000]["codec"], res[10000]["codec"]
+    r1 = res[1000]["codec"]
     assert r1["rho"] <= 1e-5 and r1["T"] <= 1e-5 and r1["u"] <= 2e-3 and r1["q"] <= 2e-2, r1
-    assert r10["rho"] <= 1e-4 and r10["T"] <= 1e-4, r10
-    # u and q: the FP16 storage floor, guarded at about twice the measured value
-    assert r10["u"] <= 6e-3 and r10["q"] <= 3e-2, r10
+    res = A.codec_accuracy(w, prec, [100], stream=s.cuda_stream, runs=("codec", "floor"),
+                           ref_arith=lbm.LBM_ARITH_FLOAT_PAIR)
+    codec, floor = res[100]["codec"], res[100]["floor"]
+    for k in ("rho", "u", "T", "q"):
+        assert 0 < floor[k] <= 1.1 * codec[k] and codec[k] <= 1.1 * floor[k], (k, codec, floor)
