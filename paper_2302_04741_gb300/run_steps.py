@@ -3,6 +3,7 @@ small launch sequence of the step kernel).
 
     python -m paper_2302_04741_gb300.run_steps --config rb2d --precision fp64 --steps 3
     python -m paper_2302_04741_gb300.run_steps --config rb2d --precision fp32 --steps 3 --moments 20
+    python -m paper_2302_04741_gb300.run_steps --config rb3d --precision fp32 --steps 3 --time 20
 """
 import argparse
 
@@ -29,6 +30,8 @@ def main():
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
     ap.add_argument("--arith", type=int, default=None, help="lbm_options.fp64_arith (FP64 storage)")
+    ap.add_argument("--time", type=int, default=0,
+                    help="then K more steps timed with CUDA events (MLUPS and algorithmic GB/s)")
     ap.add_argument("--moments", type=int, default=0,
                     help="then K read-outs into device memory (lbm_moments_async), timed with CUDA events")
     args = ap.parse_args()
@@ -43,6 +46,18 @@ def main():
     torch.cuda.synchronize()
     st = sim.conserved()
     print("ok", args.config, args.precision, args.steps, "mass", st[1])
+    elem = {W.FP64: 8, W.FP32_SHIFTED: 4, W.FP16_SCALED: 2}[PRECISIONS[args.precision]]
+    if args.time > 0:
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(args.time)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / args.time
+        print(f"time {args.time} x {us:.2f} us per step, {sim.N / us:.1f} MLUPS, "
+              f"{sim.N * 2 * sim.Q * elem / us / 1e3:.1f} GB/s algorithmic")
     if args.moments > 0:
         D, N = sim.D, sim.N
         rho = torch.empty(N, dtype=torch.float64, device="cuda")
@@ -60,7 +75,6 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / args.moments
-        elem = {W.FP64: 8, W.FP32_SHIFTED: 4, W.FP16_SCALED: 2}[PRECISIONS[args.precision]]
         nbytes = N * (sim.Q * elem + (2 + 2 * D) * 8)
         print(f"moments {args.moments} x {us:.2f} us per read-out, {nbytes / us / 1e3:.1f} GB/s algorithmic")
     sim.close()
